@@ -1,0 +1,392 @@
+// Internal device-side definitions of the CUDA path: tile geometry, the
+// per-image descriptor, the scratch layout, and the bit and union-find
+// primitives shared by the kernels.
+//
+// Terminology (mapped onto the paper's LSL B&W, Section 3.2):
+//   run        a maximal horizontal run of one colour inside a tile row
+//              (the paper's segment, Algorithm 1); a run never crosses a
+//              tile's left or right edge.
+//   local root the run that owns a tile-local component: the component's
+//              raster-first run inside the tile. The in-tile union-find links
+//              runs by minimum start index, the paper's union "by min"
+//              (Algorithm 2) on the tile's own label space.
+//   border root a local root whose component touches the tile's edge; only
+//              these enter the device-wide union-find, keyed by the raster
+//              index of their first pixel so that the final root of every
+//              component is its raster-first run (Algorithm 3's final root).
+//   node       a component of the whole image; node ids are 1 + the rank of
+//              the component's first pixel in raster order, 0 = exterior.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccl {
+
+constexpr int TW = 1024;               // tile width in pixels (32 words)
+constexpr int WPR = TW / 32;           // 32-bit words per tile row = lanes
+constexpr int TH = 32;                 // tile height in rows
+constexpr int TILE_PX = TH * TW;       // 32768: local pixel index fits 15 bits
+constexpr int NTHREADS = 256;          // threads of the tile kernels
+constexpr int NWARPS = NTHREADS / 32;
+constexpr int MAXR = 4096;             // local roots with on-chip feature records
+constexpr int SCAN_B = 256;            // segments per block of the node scan
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Loop limits: every retry loop of the union-finds is bounded and reports
+// CCL_ERR_ITER_LIMIT instead of spinning forever.
+constexpr int LOCAL_FIND_LIMIT = TILE_PX + 8;
+constexpr int LOCAL_UNION_LIMIT = 1 << 16;
+constexpr int GLOBAL_FIND_LIMIT = 1 << 24;
+constexpr int GLOBAL_UNION_LIMIT = 1 << 16;
+
+// Status bits (identical values to ccl_status in include/ccl.h).
+constexpr int ST_CAPACITY = 4;
+constexpr int ST_ITER = 32;
+
+// Per-image descriptor, built on the host for every analyse call.
+struct ImgDesc {
+    const uint8_t *img;
+    int32_t *fg, *bg;          // label images or null
+    int32_t *parent;           // [cap]
+    int64_t *feat;             // [7][cap]
+    int32_t *counts;           // [4]
+    int64_t cap;
+    int32_t *fill_map;         // [cap] or null
+    int64_t *filled_feat;      // [7][cap]
+    int32_t *filled_parent;    // [cap]
+    int32_t w, h, pitch;
+    int32_t TX, TY;            // tiles across and down
+    int32_t tile0;             // first flat tile of the image
+    int64_t seg0;              // first segment; segment = one tile row (y, tx)
+    int64_t node0;             // first per-node colour byte
+    int64_t ncap;              // colour bytes reserved for the image
+    int64_t hitem0, vitem0, pitem0;  // first border-merge work item of each kind
+    int64_t px0;               // first entry of the per-pixel run / root tables
+    int64_t b0;                // first entry of the per-edge-cell tables
+    int32_t vec;               // label rows 16-byte aligned: vector stores
+    int32_t pad_;
+};
+
+// Device scratch, carved out of one allocation by the host.
+struct Scratch {
+    uint32_t *fgbits;          // [segs*32] foreground bit plane, rows of TX*32 words
+    uint32_t *nodebits;        // [segs*32] 1 at the first pixel of every node
+    uint16_t *run_root;        // [pixels] root ordinal of every run, per tile
+    uint32_t *rootinfo;        // [pixels] per local root, see k_label.cu
+    int4 *tstat;               // [tiles] {runs, roots, border roots, 0}
+    uint16_t *edges;           // [edge cells] border ordinal of each edge cell's root
+    unsigned long long *gp;    // [n_img + edge cells] device-wide union-find
+    uint32_t *binfo;           // [same] root ordinal | colour << 16
+    int32_t *canon;            // [same] node id of border roots that are nodes
+    int32_t *seg_cnt;          // [segs]
+    int32_t *seg_base;         // [segs + 1]
+    int32_t *blk_sum;          // [segs / SCAN_B + 1]
+    uint8_t *node_fg;          // [sum of ncap] colour of every node
+    int32_t *img_cnt;          // [n_img][4]: [1] = foreground nodes
+    int32_t *status;           // [1] OR of status bits of the last call
+    int32_t *work;             // [8] tile counters of the persistent kernels
+};
+
+struct Batch {
+    const ImgDesc *desc;
+    int32_t n_img;
+    int32_t n_tiles;
+    int64_t n_segs;
+    int64_t n_hitems, n_vitems, n_pitems;
+    int32_t conn;
+    int32_t labels;
+    Scratch s;
+};
+
+// ------------------------------------------------------------ bit helpers
+
+__device__ __forceinline__ uint32_t mask_le(int b) { return FULL >> (31 - b); }      // bits 0..b
+__device__ __forceinline__ uint32_t mask_lt(int b) { return b ? (FULL >> (32 - b)) : 0u; }  // bits 0..b-1
+
+// 4 bytes -> 4 bits, bit j set when byte j is nonzero. The four flag bits
+// (7, 15, 23, 31) are gathered by one multiply whose partial products land
+// on distinct bit positions, so no carries occur.
+__device__ __forceinline__ uint32_t nz4(uint32_t v) {
+    uint32_t t = __vcmpne4(v, 0u) & 0x80808080u;
+    return (((t >> 7) * 0x00204081u) >> 21) & 0xFu;
+}
+
+__device__ __forceinline__ uint32_t nz16(uint4 v) {
+    return nz4(v.x) | (nz4(v.y) << 4) | (nz4(v.z) << 8) | (nz4(v.w) << 12);
+}
+
+__device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// Warp-wide exclusive prefix sum; *total receives the sum over the warp.
+__device__ __forceinline__ int warp_excl_sum(int v, int *total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(FULL, x, 31);
+    return x - v;
+}
+
+__device__ __forceinline__ int warp_incl_max(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v = max(v, y);
+    }
+    return v;
+}
+
+// Minimum over lanes strictly above this one (big when none).
+__device__ __forceinline__ int warp_suffix_min_excl(int v, int none) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_down_sync(FULL, x, o);
+        if (lane + o < 32) x = min(x, y);
+    }
+    int r = __shfl_down_sync(FULL, x, 1);
+    return lane == 31 ? none : r;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void set_status(const Batch &B, const ImgDesc &d, int bits) {
+    atomicOr(B.s.status, bits);
+    atomicOr(d.counts + 3, bits);
+}
+
+// Geometry of one tile. Per-tile tables are packed without gaps:
+//   px  first entry of the tile's run / root tables (th * tw entries: a tile
+//       has at most one run and one root per pixel), in raster order of
+//       tiles: all bands above hold TH * w pixels, tiles to the left th * TW;
+//   b   first entry of the tile's edge-cell tables (2 tw + 2 th entries: top
+//       row, bottom row, left column, right column); border roots of the
+//       tile occupy device-wide union-find slots n_img + b + ordinal.
+struct TileGeo {
+    int ty, tx, y0, x0, th, tw;
+    int64_t px, b;
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const ImgDesc &d, int lt) {
+    TileGeo g;
+    g.ty = lt / d.TX;
+    g.tx = lt - g.ty * d.TX;
+    g.y0 = g.ty * TH;
+    g.x0 = g.tx * TW;
+    g.th = min(TH, d.h - g.y0);
+    g.tw = min(TW, d.w - g.x0);
+    g.px = d.px0 + (int64_t)g.y0 * d.w + (int64_t)g.th * g.x0;
+    g.b = d.b0 + (int64_t)g.ty * (2 * (int64_t)d.w + 2 * (int64_t)TH * d.TX) + (int64_t)g.tx * (2 * TW + 2 * g.th);
+    return g;
+}
+
+__device__ __forceinline__ int edge_top(const TileGeo &g, int c) { return c; }
+__device__ __forceinline__ int edge_bottom(const TileGeo &g, int c) { return g.tw + c; }
+__device__ __forceinline__ int edge_left(const TileGeo &g, int r) { return 2 * g.tw + r; }
+__device__ __forceinline__ int edge_right(const TileGeo &g, int r) { return 2 * g.tw + g.th + r; }
+
+// Image owning flat tile t: the last image whose tile0 <= t.
+__device__ __forceinline__ int image_of_tile(const Batch &B, int t) {
+    int lo = 0, hi = B.n_img - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (B.desc[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// --------------------------------------------- in-tile union-find (shared)
+// Parents are 16-bit run-start indices; a root is its own parent and every
+// link points to a smaller index. Minimum-linking uses a CAS loop because
+// there is no 16-bit atomic minimum.
+
+__device__ __forceinline__ unsigned short atomic_min_u16(unsigned short *p, unsigned short v) {
+    unsigned short old = *(volatile unsigned short *)p;
+    while (old > v) {
+        unsigned short prev = atomicCAS(p, old, v);
+        if (prev == old) return old;
+        old = prev;
+    }
+    return old;
+}
+
+__device__ __forceinline__ int local_find(unsigned short *par, int a, bool *ok) {
+    for (int it = 0; it < LOCAL_FIND_LIMIT; ++it) {
+        int p = *(volatile unsigned short *)(par + a);
+        if (p == a) return a;
+        a = p;
+    }
+    *ok = false;
+    return a;
+}
+
+__device__ __forceinline__ void local_union(unsigned short *par, int a, int b, bool *ok) {
+    for (int it = 0; it < LOCAL_UNION_LIMIT; ++it) {
+        a = local_find(par, a, ok);
+        b = local_find(par, b, ok);
+        if (a == b || !*ok) return;
+        if (a < b) { int t = a; a = b; b = t; }
+        unsigned short old = atomic_min_u16(par + a, (unsigned short)b);
+        if (old == a) return;
+        a = old;
+    }
+    *ok = false;
+}
+
+// ------------------------------------------ device-wide union-find (global)
+// gp[slot] = ((key + 1) << 32) | parent_slot, key = raster index of the
+// first pixel of the slot's parent (0 for an image's exterior slot). Values
+// only decrease, so 64-bit atomicMin links a root under a smaller key, and
+// the same atomicMin halves paths safely while other threads link.
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    return *(volatile const unsigned long long *)p;
+}
+
+__device__ __forceinline__ uint32_t global_find(unsigned long long *gp, uint32_t a, bool *ok) {
+    for (int it = 0; it < GLOBAL_FIND_LIMIT; ++it) {
+        unsigned long long v = ld_volatile_u64(gp + a);
+        uint32_t p = (uint32_t)v;
+        if (p == a) return a;
+        unsigned long long vp = ld_volatile_u64(gp + p);
+        uint32_t pp = (uint32_t)vp;
+        if (pp != p) atomicMin(gp + a, vp);  // path halving: point a at its grandparent
+        a = pp;
+    }
+    *ok = false;
+    return a;
+}
+
+__device__ __forceinline__ void global_union(unsigned long long *gp, uint32_t a, uint32_t b, bool *ok) {
+    for (int it = 0; it < GLOBAL_UNION_LIMIT; ++it) {
+        a = global_find(gp, a, ok);
+        b = global_find(gp, b, ok);
+        if (a == b || !*ok) return;
+        unsigned long long va = ld_volatile_u64(gp + a), vb = ld_volatile_u64(gp + b);
+        if ((uint32_t)va != a || (uint32_t)vb != b) continue;  // linked meanwhile: retry
+        if (va < vb) {
+            uint32_t t = a; a = b; b = t;
+            unsigned long long tv = va; va = vb; vb = tv;
+        }
+        unsigned long long old = atomicMin(gp + a, vb);
+        if (old == va) return;
+        a = (uint32_t)old;
+    }
+    *ok = false;
+}
+
+
+// ------------------------------------------- feature merges in global memory
+// Features are int64 structure-of-arrays: base[f * cap + id].
+
+__device__ __forceinline__ void feat_atomic(int64_t *base, int64_t cap, int id, unsigned long long area,
+                                            unsigned long long sx, unsigned long long sy, long long xmin,
+                                            long long ymin, long long xmax, long long ymax) {
+    atomicAdd((unsigned long long *)(base + 0 * cap + id), area);
+    atomicMin((long long *)(base + 1 * cap + id), xmin);
+    atomicMin((long long *)(base + 2 * cap + id), ymin);
+    atomicMax((long long *)(base + 3 * cap + id), xmax);
+    atomicMax((long long *)(base + 4 * cap + id), ymax);
+    atomicAdd((unsigned long long *)(base + 5 * cap + id), sx);
+    atomicAdd((unsigned long long *)(base + 6 * cap + id), sy);
+}
+
+// A small open-addressing table in shared memory that combines the feature
+// contributions a CTA makes to the same node before they reach global
+// memory: a component spanning many tiles (or a survivor absorbing many
+// holes) would otherwise receive one atomic per contribution on the same
+// address. Entries that do not fit go straight to global atomics.
+constexpr int HT = 256;
+constexpr size_t HT_BYTES = (size_t)HT * (3 * 8 + 5 * 4);
+
+struct HashTab {
+    unsigned long long *area, *sx, *sy;
+    int *key, *xmin, *ymin, *xmax, *ymax;
+};
+
+__device__ __forceinline__ HashTab hash_carve(void *mem) {
+    HashTab H;
+    H.area = (unsigned long long *)mem;
+    H.sx = H.area + HT;
+    H.sy = H.sx + HT;
+    H.key = (int *)(H.sy + HT);
+    H.xmin = H.key + HT;
+    H.ymin = H.xmin + HT;
+    H.xmax = H.ymin + HT;
+    H.ymax = H.xmax + HT;
+    return H;
+}
+
+__device__ __forceinline__ void hash_init(const HashTab &H) {
+    for (int e = threadIdx.x; e < HT; e += blockDim.x) {
+        H.key[e] = -1;
+        H.area[e] = 0;
+        H.sx[e] = 0;
+        H.sy[e] = 0;
+        H.xmin[e] = INT32_MAX;
+        H.ymin[e] = INT32_MAX;
+        H.xmax[e] = -1;
+        H.ymax[e] = -1;
+    }
+}
+
+__device__ __forceinline__ void hash_push(const HashTab &H, int64_t *base, int64_t cap, int id,
+                                          unsigned long long area, unsigned long long sx, unsigned long long sy,
+                                          int xmin, int ymin, int xmax, int ymax) {
+    const uint32_t h = ((uint32_t)id * 2654435761u) >> 24;
+    for (int probe = 0; probe < 8; ++probe) {
+        const int e = (h + probe) & (HT - 1);
+        const int prev = atomicCAS(H.key + e, -1, id);
+        if (prev == -1 || prev == id) {
+            atomicAdd(H.area + e, area);
+            atomicAdd(H.sx + e, sx);
+            atomicAdd(H.sy + e, sy);
+            atomicMin(H.xmin + e, xmin);
+            atomicMin(H.ymin + e, ymin);
+            atomicMax(H.xmax + e, xmax);
+            atomicMax(H.ymax + e, ymax);
+            return;
+        }
+    }
+    feat_atomic(base, cap, id, area, sx, sy, xmin, ymin, xmax, ymax);
+}
+
+__device__ __forceinline__ void hash_flush(const HashTab &H, int64_t *base, int64_t cap) {
+    for (int e = threadIdx.x; e < HT; e += blockDim.x) {
+        const int id = H.key[e];
+        if (id >= 0) feat_atomic(base, cap, id, H.area[e], H.sx[e], H.sy[e], H.xmin[e], H.ymin[e], H.xmax[e], H.ymax[e]);
+    }
+}
+
+// --------------------------------------------------------- host launchers
+struct LaunchCfg {
+    int sms;
+};
+
+void launch_prologue(const Batch &B, cudaStream_t st);
+void launch_label(const Batch &B, const LaunchCfg &c, cudaStream_t st);
+void launch_merge(const Batch &B, cudaStream_t st);
+void launch_resolve(const Batch &B, const LaunchCfg &c, cudaStream_t st);
+void launch_scan(const Batch &B, cudaStream_t st);
+void launch_canon(const Batch &B, const LaunchCfg &c, cudaStream_t st);
+void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st);
+void launch_fill(const Batch &B, int64_t area_threshold, const LaunchCfg &c, cudaStream_t st);
+cudaError_t configure_label();
+cudaError_t configure_write();
+
+}  // namespace ccl

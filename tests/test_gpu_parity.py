@@ -1,0 +1,208 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything is integer and the result is unique (canonical node ids), so the
+bar is bit-exact equality of the label images, the tree, the int64 features,
+the counts and the hole-filling outputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import reference as orc
+from paper_2006_09299_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+INT64_MAX = np.iinfo(np.int64).max
+
+
+@pytest.fixture(scope="module")
+def ccl():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2006_09299_gb300 import ccl as m
+    return m
+
+
+def to_dev(padded):
+    return torch.from_numpy(np.ascontiguousarray(padded)).cuda()
+
+
+def run_single(ccl, padded, w, conn=0, labels=True, fills=()):
+    h, pitch = padded.shape
+    ctx = ccl.Context(w, h, pitch, conn=conn)
+    out = ctx.analyze(to_dev(padded), labels=labels)
+    res = {}
+    n, nfg, nbg, st = ctx.get_counts()
+    res.update(n=n, counts=(n, nfg, nbg), status=st,
+               parent=out.parent[:n].cpu().numpy(), feat=out.features[:, :n].cpu().numpy())
+    if labels:
+        res["fg"] = out.fg.cpu().numpy()
+        res["bg"] = out.bg.cpu().numpy()
+    res["fills"] = {}
+    for T in fills:
+        ctx.fill_holes(T)
+        torch.cuda.synchronize()
+        res["fills"][T] = (out.fill_map[:n].cpu().numpy(), out.filled_features[:, :n].cpu().numpy(),
+                           out.filled_parent[:n].cpu().numpy())
+    st2 = ctx.get_counts()[3]
+    res["status"] |= st2
+    ctx.close()
+    return res
+
+
+def oracle_cap(w, h):
+    return min(orc.capacity(w, h), max(4096, (w * h) // 4))
+
+
+def run_oracle(padded, w, conn=0):
+    h = padded.shape[0]
+    try:
+        return orc.analyze(padded, w=w, conn=conn, cap=oracle_cap(w, h))
+    except RuntimeError:
+        return orc.analyze(padded, w=w, conn=conn)
+
+
+def assert_parity(g, r, labels=True, fills=()):
+    assert g["status"] == 0, g["status"]
+    assert g["n"] == r["n"]
+    assert g["counts"] == (int(r["counts"][0]), int(r["counts"][1]), int(r["counts"][2]))
+    if labels:
+        np.testing.assert_array_equal(g["fg"], r["fg"])
+        np.testing.assert_array_equal(g["bg"], r["bg"])
+    np.testing.assert_array_equal(g["parent"], r["parent"])
+    np.testing.assert_array_equal(g["feat"], r["feat"])
+    for T in fills:
+        fmap, ff, fpar = orc.fill(r, T)
+        gm, gf, gp = g["fills"][T]
+        np.testing.assert_array_equal(gm, fmap)
+        np.testing.assert_array_equal(gf, ff)
+        np.testing.assert_array_equal(gp, fpar)
+
+
+SIZES = [(1, 1), (1, 2), (2, 1), (3, 40), (15, 17), (31, 33), (32, 32), (33, 1023), (64, 1024),
+         (65, 1025), (70, 2049), (100, 3000), (257, 1100), (40, 4100)]
+
+
+@pytest.mark.parametrize("kind", inputs.ADVERSARIAL_KINDS)
+def test_adversarial_shapes(ccl, kind):
+    for h, w in SIZES:
+        img = inputs.adversarial(h, w, kind)
+        pitch = -(-w // 16) * 16
+        padded = inputs.pitched(img, pitch)
+        g = run_single(ccl, padded, w, fills=(0, 3, INT64_MAX))
+        assert_parity(g, run_oracle(padded, w), fills=(0, 3, INT64_MAX))
+
+
+@pytest.mark.parametrize("conn", [0, 1])
+@pytest.mark.parametrize("case", range(8))
+def test_random_multi_tile(ccl, conn, case):
+    rng = np.random.default_rng(900 + case)
+    h = int(rng.integers(30, 200))
+    w = int(rng.integers(900, 3300))
+    d = [0.1, 0.3, 0.5, 0.7, 0.9, 0.45, 0.55, 0.62][case]
+    g = [1, 1, 1, 1, 1, 2, 3, 4][case]
+    img = inputs.granular(h, w, d, g, case)
+    pitch = -(-w // 16) * 16 + 16 * int(rng.integers(0, 3))
+    padded = inputs.pitched(img * np.uint8(1 + 254 * (case % 2)), pitch)
+    res = run_single(ccl, padded, w, conn=conn, fills=(-1, 2, 64, INT64_MAX))
+    assert_parity(res, run_oracle(padded, w, conn), fills=(-1, 2, 64, INT64_MAX))
+
+
+def test_config1_512(ccl):
+    img = inputs.bernoulli(512, 512, 0.5, 1)
+    g = run_single(ccl, img, 512, fills=(64, INT64_MAX))
+    assert_parity(g, run_oracle(img, 512), fills=(64, INT64_MAX))
+
+
+def test_labels_off(ccl):
+    img = inputs.granular(300, 2500, 0.5, 2, 5)
+    padded = inputs.pitched(img, 2512)
+    g = run_single(ccl, padded, 2500, labels=False, fills=(10,))
+    assert_parity(g, run_oracle(padded, 2500), labels=False, fills=(10,))
+
+
+def test_context_reuse_and_graph_replay(ccl):
+    h, w = 130, 2000
+    ctx = ccl.Context(w, h, 2000)
+    out = ctx.new_outputs()
+    for seed in range(4):
+        img = inputs.granular(h, w, 0.3 + 0.1 * seed, 1 + seed, seed)
+        ctx.analyze(to_dev(img), out=out)
+        n, nfg, nbg, st = ctx.get_counts()
+        r = run_oracle(img, w)
+        assert st == 0 and n == r["n"]
+        np.testing.assert_array_equal(out.fg.cpu().numpy(), r["fg"])
+        np.testing.assert_array_equal(out.features[:, :n].cpu().numpy(), r["feat"])
+        np.testing.assert_array_equal(out.parent[:n].cpu().numpy(), r["parent"])
+    ctx.close()
+
+
+def test_batched_equals_oracle_and_single(ccl):
+    batch = inputs.uneven_batch(seed=4, n=24, lo=16, hi=1500)
+    imgs = [(to_dev(p), w) for p, w in batch]
+    tot = sum(p.shape[0] * w for p, w in batch)
+    bctx = ccl.BatchContext(len(batch), tot, 1500)
+    outs = bctx.analyze(imgs, fill=True)
+    bctx.fill_holes(20)
+    torch.cuda.synchronize()
+    for (p, w), o in zip(batch, outs):
+        r = run_oracle(p, w)
+        n = o.n
+        assert o.status() == 0
+        assert n == r["n"]
+        np.testing.assert_array_equal(o.fg.cpu().numpy(), r["fg"])
+        np.testing.assert_array_equal(o.bg.cpu().numpy(), r["bg"])
+        np.testing.assert_array_equal(o.parent[:n].cpu().numpy(), r["parent"])
+        np.testing.assert_array_equal(o.features[:, :n].cpu().numpy(), r["feat"])
+        fmap, ff, fpar = orc.fill(r, 20)
+        np.testing.assert_array_equal(o.fill_map[:n].cpu().numpy(), fmap)
+        np.testing.assert_array_equal(o.filled_features[:, :n].cpu().numpy(), ff)
+        np.testing.assert_array_equal(o.filled_parent[:n].cpu().numpy(), fpar)
+    # the same batch again (graph replay) gives the same result
+    outs2 = bctx.analyze(imgs)
+    torch.cuda.synchronize()
+    for o, o2 in zip(outs, outs2):
+        assert torch.equal(o.fg, o2.fg) and torch.equal(o.counts[:3], o2.counts[:3])
+    bctx.close()
+
+
+def test_capacity_error_reported_on_device(ccl):
+    img = inputs.adversarial(64, 64, "checker0")
+    d = to_dev(img)
+    bctx = ccl.BatchContext(1, 64 * 64, 64)
+    o = ccl.Analysis(64, 64, 100, True, "cuda")   # far fewer slots than nodes
+    bctx.analyze([(d, 64)], outs=[o])
+    torch.cuda.synchronize()
+    assert o.status() & ccl.ERR_CAPACITY
+    r = run_oracle(img, 64)
+    assert o.n == r["n"]
+    np.testing.assert_array_equal(o.fg.cpu().numpy(), r["fg"])   # labels are still right
+    bctx.close()
+
+
+def test_bad_alignment_is_rejected(ccl):
+    buf = torch.zeros(64 * 64 + 16, dtype=torch.uint8, device="cuda")
+    bctx = ccl.BatchContext(1, 64 * 64, 64)
+    o = ccl.Analysis(64, 64, ccl.node_capacity(64, 64), True, "cuda")
+    with pytest.raises(ccl.CCLError) as e:
+        bctx.analyze([(buf[1:1 + 64 * 64].view(64, 64), 64)], outs=[o])
+    assert e.value.status == ccl.ERR_ALIGN
+    bctx.close()
+
+
+# ------------------------------------------------------------ full sizes
+
+
+def test_sweep_4096_selected(ccl):
+    """Density x granularity sweep at full size: g = 1 (the worst case) and
+    two coarser images, compared element by element."""
+    for i_d, i_g in [(2, 0), (3, 0), (4, 2), (0, 4)]:
+        img = inputs.sweep_image(i_d, i_g)
+        g = run_single(ccl, img, 4096, fills=(64,))
+        assert_parity(g, run_oracle(img, 4096), fills=(64,))
+
+
+def test_rings_8192_full(ccl):
+    img = inputs.rings()
+    g = run_single(ccl, img, 8192, fills=(64,))
+    assert_parity(g, run_oracle(img, 8192), fills=(64,))
