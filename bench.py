@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 connected component analysis.
+
+Default workload (--workload sweep4096): the density x granularity sweep,
+25 uint8 images of 4096 x 4096 (densities 0.1-0.9 x granularities 1-16).
+One step = one batched analysis of all 25 images (fg + bg label images, tree,
+int64 features) followed by hole filling with area threshold 64, i.e. every
+step of the hot path once. Metric: Gpixel/s over the whole job.
+
+Other workloads: rings8192 (one 8192 x 8192 structured image + fill 64),
+uneven256 (256 images of uneven sizes, batched). The default line also
+carries the batched-vs-plain ratio measured on uneven256.
+
+--impl reference times the CPU oracle (flood fill, one host thread) on the
+same workload and metric, a bounded sample of images per step.
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpixel/s fg+bg labels+tree+features; % HBM roofline; batched vs plain"
+FILL_T = 64
+LABEL_BYTES_PER_PX = 8      # fg + bg int32 label writes
+IMAGE_BYTES_PER_PX = 1      # uint8 read
+PATH_BYTES_PER_PX = IMAGE_BYTES_PER_PX + LABEL_BYTES_PER_PX
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ inputs
+
+
+def workload_images(name):
+    from paper_2006_09299_gb300 import inputs
+    if name == "sweep4096":
+        return [(inputs.sweep_image(i, j), 4096) for i in range(5) for j in range(5)]
+    if name == "rings8192":
+        return [(inputs.rings(), 8192)]
+    if name == "uneven256":
+        return inputs.uneven_batch(seed=4, n=256)
+    raise ValueError(name)
+
+
+def workload_desc(name, imgs):
+    px = sum(p.shape[0] * w for p, w in imgs)
+    if name == "sweep4096":
+        return {"workload": "density x granularity sweep: 25 uint8 images 4096x4096, d in {0.1..0.9} x g in {1,2,4,8,16}",
+                "images": 25, "pixels_per_step": px, "fill_area_threshold": FILL_T,
+                "connectivity": "8-fg / 4-bg", "l2": "inputs larger than L2 (400 MiB read, 3.2 GiB written per step)"}
+    if name == "rings8192":
+        return {"workload": "8192x8192 uint8 rings image: 2000 concentric ring sets over 5% salt noise",
+                "images": 1, "pixels_per_step": px, "fill_area_threshold": FILL_T,
+                "connectivity": "8-fg / 4-bg", "l2": "inputs larger than L2 (64 MiB read, 512 MiB written per step)"}
+    return {"workload": "uneven batch: 256 uint8 images, sides log-uniform 64..2048, pitch padded to 128",
+            "images": len(imgs), "pixels_per_step": px, "fill_area_threshold": FILL_T,
+            "connectivity": "8-fg / 4-bg", "l2": "inputs larger than L2 (~100 MiB read, ~800 MiB written per step)"}
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+
+
+def kernel_source_hash(name):
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_2006_09299_gb300", "csrc", name), "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_file, workload, units):
+    """DRAM bytes per launch from the committed ncu summary, scaled by units,
+    or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p)).get(kernel_file, {})
+    if rec.get("source_sha256_16") != kernel_source_hash(kernel_file):
+        return None
+    per_px = rec.get("dram_bytes_per_pixel", {}).get(workload)
+    return None if per_px is None else per_px * units
+
+
+# ------------------------------------------------------------------ our arm
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__ as ge
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        ge.build()
+    if world > 1:
+        torch.distributed.barrier()   # the other ranks load what rank 0 built
+    from paper_2006_09299_gb300 import ccl
+    imgs = workload_images(args.workload)
+    if args.subset:
+        imgs = imgs[: args.subset]
+    px = sum(p.shape[0] * w for p, w in imgs)
+    d_imgs = [(torch.from_numpy(np.ascontiguousarray(p)).to(dev), w) for p, w in imgs]
+    max_side = max(max(p.shape[0], w) for p, w in imgs)
+    ctx = ccl.BatchContext(len(imgs), px, max_side)
+    shapes = [(w, p.shape[0]) for p, w in imgs]
+    if args.tight:
+        # node arrays sized to a quarter of the pixels instead of the worst-case
+        # bound (keeps profiler captures small; overflow would be reported)
+        outs = [ccl.Analysis(w, h, max(4096, w * h // 4), True, dev).alloc_fill() for w, h in shapes]
+    else:
+        outs = ctx.new_outputs(shapes, labels=True, fill=True, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.analyze(d_imgs, outs=outs)
+        ctx.fill_holes(FILL_T)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    status = max(o.status() for o in outs)
+    if status:
+        raise RuntimeError("device status %d during warm-up" % status)
+
+    # ---- timed region: K steps, back to back, CUDA events on the stream
+    launches0 = ctx.launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    launches = ctx.launch_count() - launches0
+    clocks = clk.summary()
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * px / (ms * 1e-3) / 1e9
+
+    # ---- per-kernel device time over a second timed region (phase events)
+    ctx.enable_phase_timing(2 * args.steps)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        step()
+    phases = ctx.read_phase_timing()
+    ctx.enable_phase_timing(0)
+    per = {k: (v[0] / v[1] if v[1] else 0.0) for k, v in phases.items()}
+    peak, peak_kind = measured_peaks()
+    dominant = max(per, key=per.get)
+    bytes_per_px = {"write": LABEL_BYTES_PER_PX, "label": IMAGE_BYTES_PER_PX}.get(dominant)
+    kernel_file = {"write": "k_write.cu", "label": "k_label.cu"}.get(dominant)
+    roofline = None
+    if bytes_per_px is not None:
+        alg = bytes_per_px * px
+        achieved = alg / (per[dominant] * 1e-3) / 1e9
+        traffic = recorded_traffic(kernel_file, args.workload, px)
+        roofline = {"bound": "hbm", "kernel": "k_" + dominant, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "algorithmic_bytes": alg, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                    "avg_launch_ms": round(per[dominant], 4)}
+    path_gbs = PATH_BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    e2e = None if args.no_e2e else run_e2e(args, ctx, imgs, outs, dev, stream, px)
+
+    extra = {}
+    if args.workload == "sweep4096" and not args.no_extra:
+        extra["batched_vs_plain"] = batched_vs_plain(ccl, dev, stream)
+
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded generators shaped like the paper's workloads)",
+        "config": dict(workload_desc(args.workload, imgs), parallelism="replicas" if world > 1 else "single"),
+        "roofline": roofline,
+        "path_roofline": {"bytes_per_pixel": PATH_BYTES_PER_PX, "achieved": round(path_gbs, 1), "peak": peak,
+                          "unit": "GB/s", "frac": round(path_gbs / peak, 4)},
+        "phase_ms": {k: round(v, 4) for k, v in per.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    res.update(extra)
+    return res
+
+
+def run_e2e(args, ctx, imgs, outs, dev, stream, px):
+    """Same metric through the public API with host buffers: every step copies
+    the images from pinned host memory, analyses and fills, then reads the
+    counts, the label images and the node tables back to pinned host memory."""
+    import torch
+    h_imgs = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p, w in imgs]
+    d_imgs = [(torch.empty_like(t, device=dev), w) for t, (p, w) in zip(h_imgs, imgs)]
+    h_fg = [torch.empty_like(o.fg, device="cpu").pin_memory() for o in outs]
+    h_bg = [torch.empty_like(o.bg, device="cpu").pin_memory() for o in outs]
+    h_cnt = torch.empty((len(outs), 4), dtype=torch.int32).pin_memory()
+    nmax = [o.n for o in outs]   # node counts of this workload (host buffers sized to them)
+    h_par = [torch.empty(c, dtype=torch.int32).pin_memory() for c in nmax]
+    h_feat = [torch.empty((7, c), dtype=torch.int64).pin_memory() for c in nmax]
+    steps = max(1, min(args.steps, 5))
+    h2d = d2h = 0
+
+    def one():
+        nonlocal h2d, d2h
+        b_in = b_out = 0
+        for (d, _), h in zip(d_imgs, h_imgs):
+            d.copy_(h, non_blocking=True)
+            b_in += h.numel()
+        ctx.analyze(d_imgs, outs=outs)
+        ctx.fill_holes(FILL_T)
+        for i, o in enumerate(outs):
+            h_cnt[i].copy_(o.counts, non_blocking=True)
+        stream.synchronize()
+        b_out += h_cnt.numel() * 4
+        for i, o in enumerate(outs):
+            n = int(h_cnt[i, 0])
+            h_fg[i].copy_(o.fg, non_blocking=True)
+            h_bg[i].copy_(o.bg, non_blocking=True)
+            h_par[i][:n].copy_(o.parent[:n], non_blocking=True)
+            h_feat[i][:, :n].copy_(o.features[:, :n], non_blocking=True)
+            b_out += 2 * o.fg.numel() * 4 + n * 4 + 7 * n * 8
+        stream.synchronize()
+        h2d, d2h = b_in, b_out
+
+    one()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": round(px / dt / 1e9, 3), "unit": "Gpixel/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "includes": "H2D images, analyse + fill, D2H counts, fg/bg labels, tree and features"}
+
+
+def batched_vs_plain(ccl, dev, stream, reps=5):
+    """uneven256: one batched call (graph replay) vs the same images analysed
+    one call per image, same GPU, same outputs."""
+    import torch
+    from paper_2006_09299_gb300 import inputs
+    imgs = inputs.uneven_batch(seed=4, n=256)
+    px = sum(p.shape[0] * w for p, w in imgs)
+    d_imgs = [(torch.from_numpy(p).to(dev), w) for p, w in imgs]
+    shapes = [(w, p.shape[0]) for p, w in imgs]
+    bctx = ccl.BatchContext(len(imgs), px, 2048)
+    outs = bctx.new_outputs(shapes, labels=True, fill=False, device=dev)
+    pctx = ccl.BatchContext(1, 2048 * 2048, 2048, graph_cache=False)
+
+    def batched():
+        bctx.analyze(d_imgs, outs=outs)
+
+    def plain():
+        for di, o in zip(d_imgs, outs):
+            pctx.analyze([di], outs=[o])
+
+    res = {}
+    for name, fn in (("batched", batched), ("plain", plain)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / reps
+    bctx.close()
+    pctx.close()
+    return {"workload": "uneven256 (256 images, %.1f Mpx)" % (px / 1e6),
+            "batched_ms": round(res["batched"], 3), "plain_ms": round(res["plain"], 3),
+            "batched_gpx_s": round(px / res["batched"] / 1e6, 2), "plain_gpx_s": round(px / res["plain"] / 1e6, 2),
+            "ratio": round(res["plain"] / res["batched"], 2)}
+
+
+# ------------------------------------------------------------ reference arm
+
+
+def oracle_rate(imgs, budget_s, max_images=None):
+    """Time the oracle (as it stands) on images until budget_s elapses."""
+    from oracle import reference as orc
+    orc.build()
+    done_px, t_total, names = 0, 0.0, 0
+    for p, w in imgs[: max_images or len(imgs)]:
+        h = p.shape[0]
+        t = time.perf_counter()
+        try:
+            orc.analyze(p, w=w, cap=max(4096, (w * h) // 4))
+        except RuntimeError:
+            orc.analyze(p, w=w)
+        t_total += time.perf_counter() - t
+        done_px += w * h
+        names += 1
+        if t_total >= budget_s:
+            break
+    return done_px / t_total / 1e9, names, done_px, t_total
+
+
+def cpu_baseline(imgs, budget_s=12.0):
+    rate, n, dpx, t = oracle_rate(imgs, budget_s)
+    return {"value": round(rate, 5), "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of %d images of the workload (%.1f Mpx, %.1f s), C flood-fill oracle, 1 host thread"
+                      % (n, len(imgs), dpx / 1e6, t)}
+
+
+def run_reference(args, rank, world):
+    imgs = workload_images(args.workload)
+    px = sum(p.shape[0] * w for p, w in imgs)
+    # bounded sample per step: rotate through the images, ~budget per step
+    per_step = max(1, min(len(imgs), 2))
+    rates = []
+    for s in range(args.warmup + args.steps):
+        sample = [imgs[(s * per_step + k) % len(imgs)] for k in range(per_step)]
+        rate, n, dpx, t = oracle_rate(sample, 1e9)
+        if s >= args.warmup:
+            rates.append((dpx, t))
+    dpx = sum(a for a, b in rates)
+    t = sum(b for a, b in rates)
+    value = dpx / t / 1e9
+    ms = px / (value * 1e9) * 1e3
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded generators shaped like the paper's workloads)",
+        "config": workload_desc(args.workload, imgs),
+        "cpu_baseline": {"value": round(value, 5), "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d images per step of the workload, C flood-fill oracle, 1 host thread" % per_step},
+        "e2e": {"value": round(value, 5), "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep4096", choices=["sweep4096", "rings8192", "uneven256"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--subset", type=int, default=0, help="use only the first k images of the workload")
+    ap.add_argument("--tight", action="store_true", help="node arrays sized w*h/4 instead of the bound")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = dist_env()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(workload_images(args.workload))
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

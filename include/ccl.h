@@ -182,8 +182,39 @@ ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, i
 /* Hole filling for every image of the last batch that has fill buffers. */
 ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stream_t stream);
 
-/* Enable (1) or disable (0) the CUDA-graph cache of ccl_analyze_batched. */
+/* Enable (1) or disable (0) the CUDA-graph cache of ccl_analyze_batched and
+ * ccl_analyze. */
 ccl_status ccl_set_graph_cache(ccl_ctx *ctx, int32_t enable);
+
+/* ------------------------------------------------------- instrumentation */
+
+/* Phases of one analysis and of one hole filling, in launch order. */
+enum {
+    CCL_PHASE_PROLOGUE = 0,  /* per-image counters and the exterior node */
+    CCL_PHASE_LABEL = 1,     /* runs and in-tile union-find (Algorithms 1, 2) */
+    CCL_PHASE_MERGE = 2,     /* cross-tile and exterior links (Algorithm 2) */
+    CCL_PHASE_RESOLVE = 3,   /* final roots of tile-border parts (Algorithm 3) */
+    CCL_PHASE_SCAN = 4,      /* raster-order node numbering */
+    CCL_PHASE_CANON = 5,     /* node ids of multi-tile components */
+    CCL_PHASE_WRITE = 6,     /* labels, features, tree (Algorithms 3, 4) */
+    CCL_PHASE_FILL_MAP = 7,  /* hole filling: survivors (Algorithm 3) */
+    CCL_PHASE_FILL_MERGE = 8,/* hole filling: feature merge */
+    CCL_PHASE_COUNT = 9
+};
+
+/* Record CUDA events between the phases of the next max_calls analyse / fill
+ * calls (0 turns recording off). While recording, calls launch their
+ * kernels directly instead of replaying a graph. */
+ccl_status ccl_enable_phase_timing(ccl_ctx *ctx, int32_t max_calls);
+
+/* Wait for the recorded calls and return, per phase, the summed device time
+ * in milliseconds and the number of timed launches of that phase
+ * (arrays of CCL_PHASE_COUNT). Clears the records. */
+ccl_status ccl_read_phase_timing(ccl_ctx *ctx, double *total_ms, int64_t *count);
+
+/* Number of kernels this context has enqueued since it was created
+ * (graph replays count the kernels they contain). */
+ccl_status ccl_get_launch_count(ccl_ctx *ctx, int64_t *launches);
 
 const char *ccl_status_string(ccl_status status);
 

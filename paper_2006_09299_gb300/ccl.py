@@ -48,6 +48,9 @@ SIGNATURES = {
     "ccl_analyze_batched": (ctypes.c_int, [_p, ctypes.POINTER(ImageDesc), _i32, _p]),
     "ccl_fill_holes_batched": (ctypes.c_int, [_p, _i64, _p]),
     "ccl_set_graph_cache": (ctypes.c_int, [_p, _i32]),
+    "ccl_enable_phase_timing": (ctypes.c_int, [_p, _i32]),
+    "ccl_read_phase_timing": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
+    "ccl_get_launch_count": (ctypes.c_int, [_p, ctypes.POINTER(_i64)]),
     "ccl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ccl_destroy": (None, [_p]),
 }
@@ -85,6 +88,31 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+PHASES = ("prologue", "label", "merge", "resolve", "scan", "canon", "write", "fill_map", "fill_merge")
+
+
+class _Instrumented:
+    """Phase timing and launch counting shared by both context kinds."""
+
+    def enable_phase_timing(self, max_calls):
+        _check(_lib.ccl_enable_phase_timing(self._h, int(max_calls)), "ccl_enable_phase_timing")
+
+    def read_phase_timing(self):
+        """{phase: (total_ms, launches)} of the recorded calls (waits)."""
+        ms = (ctypes.c_double * len(PHASES))()
+        cnt = (_i64 * len(PHASES))()
+        _check(_lib.ccl_read_phase_timing(self._h, ms, cnt), "ccl_read_phase_timing")
+        return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+    def launch_count(self):
+        n = _i64()
+        _check(_lib.ccl_get_launch_count(self._h, ctypes.byref(n)), "ccl_get_launch_count")
+        return n.value
+
+    def set_graph_cache(self, enable):
+        _check(_lib.ccl_set_graph_cache(self._h, 1 if enable else 0), "ccl_set_graph_cache")
+
+
 class Analysis:
     """Outputs of one analysed image (device tensors). Node arrays have the
     full capacity; `n` (which waits for the stream) gives the node count."""
@@ -113,7 +141,7 @@ class Analysis:
         return int(self.counts[3].item())
 
 
-class Context:
+class Context(_Instrumented):
     """ccl_create / ccl_analyze / ccl_fill_holes for images of one shape."""
 
     def __init__(self, w, h, pitch=None, conn=CONN_8FG_4BG):
@@ -167,7 +195,7 @@ class Context:
             pass
 
 
-class BatchContext:
+class BatchContext(_Instrumented):
     """ccl_create_batched / ccl_analyze_batched / ccl_fill_holes_batched."""
 
     def __init__(self, max_images, max_total_pixels, max_side, conn=CONN_8FG_4BG, graph_cache=True):

@@ -91,7 +91,18 @@ struct ccl_ctx {
     cudaStream_t last_stream = nullptr;
     bool graph_cache = true;
     std::map<Shape, Graph> graphs;
+    // instrumentation
+    int64_t launches = 0;
+    std::vector<std::vector<cudaEvent_t>> timing;  // one event set per timed call
+    std::vector<int> timing_kind;                  // 0 analyse, 1 fill
+    size_t timing_used = 0;
 };
+
+// Kernels per analysis (prologue, label, merge, resolve, 3 scan, canon, write)
+// and per hole filling (map, merge).
+constexpr int ANALYSE_KERNELS = 9;
+constexpr int FILL_KERNELS = 2;
+constexpr int ANALYSE_PHASES = 7;
 
 constexpr int RING = 8;
 
@@ -249,15 +260,35 @@ static Batch make_batch(const ccl_ctx *c, const Plan &P) {
     return B;
 }
 
-static void enqueue_analysis(const Batch &B, cudaStream_t st) {
+// Enqueue the phases; ev (optional) receives ANALYSE_PHASES + 1 events
+// around them.
+static void enqueue_analysis(const Batch &B, cudaStream_t st, const cudaEvent_t *ev = nullptr) {
     const LaunchCfg lc{g_sms};
+    auto mark = [&](int k) {
+        if (ev) cudaEventRecord(ev[k], st);
+    };
+    mark(0);
     launch_prologue(B, st);
+    mark(1);
     launch_label(B, lc, st);
+    mark(2);
     launch_merge(B, st);
+    mark(3);
     launch_resolve(B, lc, st);
+    mark(4);
     launch_scan(B, st);
+    mark(5);
     launch_canon(B, lc, st);
+    mark(6);
     launch_write(B, lc, st);
+    mark(7);
+}
+
+// Event set for the next timed call of the given kind, or null.
+static const cudaEvent_t *timing_slot(ccl_ctx *c, int kind) {
+    if (c->timing_used >= c->timing.size()) return nullptr;
+    c->timing_kind[c->timing_used] = kind;
+    return c->timing[c->timing_used++].data();
 }
 
 static Shape shape_of(const ccl_ctx *c, const Plan &P) {
@@ -293,6 +324,8 @@ static ccl_status run_plan(ccl_ctx *c, const Plan &P, cudaStream_t st, bool use_
     const Batch B = make_batch(c, P);
     cudaError_t e = upload_plan(c, P, st);
     if (e != cudaSuccess) return CCL_ERR_CUDA;
+    const cudaEvent_t *ev = timing_slot(c, 0);
+    if (ev) use_graph = false;
     if (use_graph) {
         const Shape key = shape_of(c, P);
         auto it = c->graphs.find(key);
@@ -316,10 +349,11 @@ static ccl_status run_plan(ccl_ctx *c, const Plan &P, cudaStream_t st, bool use_
         }
         e = cudaGraphLaunch(it->second.exec, st);
     } else {
-        enqueue_analysis(B, st);
+        enqueue_analysis(B, st, ev);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return CCL_ERR_CUDA;
+    c->launches += ANALYSE_KERNELS;
     c->last = P;
     c->have_last = true;
     c->last_stream = st;
@@ -389,8 +423,9 @@ static ccl_status fill_last(ccl_ctx *ctx, int64_t T, cudaStream_t st) {
     const Plan &P = ctx->last;
     cudaError_t e = upload_plan(ctx, P, st);
     if (e != cudaSuccess) return CCL_ERR_CUDA;
-    launch_fill(make_batch(ctx, P), T, LaunchCfg{g_sms}, st);
+    launch_fill(make_batch(ctx, P), T, LaunchCfg{g_sms}, st, timing_slot(ctx, 1));
     e = cudaGetLastError();
+    ctx->launches += FILL_KERNELS;
     ctx->last_stream = st;
     return from_cuda(e);
 }
@@ -459,6 +494,66 @@ ccl_status ccl_set_graph_cache(ccl_ctx *ctx, int32_t enable) {
     return CCL_OK;
 }
 
+static void free_timing(ccl_ctx *ctx) {
+    for (auto &set : ctx->timing)
+        for (cudaEvent_t e : set)
+            if (e) cudaEventDestroy(e);
+    ctx->timing.clear();
+    ctx->timing_kind.clear();
+    ctx->timing_used = 0;
+}
+
+ccl_status ccl_enable_phase_timing(ccl_ctx *ctx, int32_t max_calls) {
+    if (!ctx || max_calls < 0) return CCL_ERR_ARG;
+    if (ctx->have_last) cudaStreamSynchronize(ctx->last_stream);
+    free_timing(ctx);
+    ctx->timing.assign(max_calls, std::vector<cudaEvent_t>(ANALYSE_PHASES + 1, nullptr));
+    ctx->timing_kind.assign(max_calls, 0);
+    for (auto &set : ctx->timing)
+        for (cudaEvent_t &e : set)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                free_timing(ctx);
+                return CCL_ERR_CUDA;
+            }
+    return CCL_OK;
+}
+
+ccl_status ccl_read_phase_timing(ccl_ctx *ctx, double *total_ms, int64_t *count) {
+    if (!ctx || !total_ms || !count) return CCL_ERR_ARG;
+    for (int k = 0; k < CCL_PHASE_COUNT; ++k) {
+        total_ms[k] = 0.0;
+        count[k] = 0;
+    }
+    for (size_t i = 0; i < ctx->timing_used; ++i) {
+        const std::vector<cudaEvent_t> &ev = ctx->timing[i];
+        if (cudaEventSynchronize(ev[ctx->timing_kind[i] == 0 ? ANALYSE_PHASES : 2]) != cudaSuccess)
+            return CCL_ERR_CUDA;
+        if (ctx->timing_kind[i] == 0) {
+            for (int k = 0; k < ANALYSE_PHASES; ++k) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return CCL_ERR_CUDA;
+                total_ms[k] += ms;
+                count[k] += 1;
+            }
+        } else {
+            for (int k = 0; k < 2; ++k) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) return CCL_ERR_CUDA;
+                total_ms[CCL_PHASE_FILL_MAP + k] += ms;
+                count[CCL_PHASE_FILL_MAP + k] += 1;
+            }
+        }
+    }
+    ctx->timing_used = 0;
+    return CCL_OK;
+}
+
+ccl_status ccl_get_launch_count(ccl_ctx *ctx, int64_t *launches) {
+    if (!ctx || !launches) return CCL_ERR_ARG;
+    *launches = ctx->launches;
+    return CCL_OK;
+}
+
 const char *ccl_status_string(ccl_status s) {
     switch ((int)s) {
         case CCL_OK: return "ok";
@@ -476,6 +571,7 @@ const char *ccl_status_string(ccl_status s) {
 void ccl_destroy(ccl_ctx *ctx) {
     if (!ctx) return;
     if (ctx->last_stream || ctx->have_last) cudaStreamSynchronize(ctx->last_stream);
+    free_timing(ctx);
     for (auto &kv : ctx->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     for (int k = 0; k < RING; ++k)

@@ -385,7 +385,8 @@ void launch_resolve(const Batch &B, const LaunchCfg &c, cudaStream_t st);
 void launch_scan(const Batch &B, cudaStream_t st);
 void launch_canon(const Batch &B, const LaunchCfg &c, cudaStream_t st);
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st);
-void launch_fill(const Batch &B, int64_t area_threshold, const LaunchCfg &c, cudaStream_t st);
+void launch_fill(const Batch &B, int64_t area_threshold, const LaunchCfg &c, cudaStream_t st,
+                 const cudaEvent_t *ev = nullptr);
 cudaError_t configure_label();
 cudaError_t configure_write();
 

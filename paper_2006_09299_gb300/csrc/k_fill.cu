@@ -110,11 +110,14 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
     hash_flush(H, d.filled_feat, cap);
 }
 
-void launch_fill(const Batch &B, int64_t T, const LaunchCfg &c, cudaStream_t st) {
+void launch_fill(const Batch &B, int64_t T, const LaunchCfg &c, cudaStream_t st, const cudaEvent_t *ev) {
     const int bx = max(1, (4 * c.sms + B.n_img - 1) / B.n_img);
     const dim3 grid(bx, B.n_img);
+    if (ev) cudaEventRecord(ev[0], st);
     k_fill_map<<<grid, 256, 0, st>>>(B, T);
+    if (ev) cudaEventRecord(ev[1], st);
     k_fill_merge<<<grid, 256, 0, st>>>(B);
+    if (ev) cudaEventRecord(ev[2], st);
 }
 
 }  // namespace ccl
