@@ -181,6 +181,8 @@ def run_ours(args, rank, world, local_rank):
     imgs = workload_images(args.workload)
     if args.subset:
         imgs = imgs[: args.subset]
+    if args.pick:
+        imgs = [imgs[int(i)] for i in args.pick.split(",")]
     px = sum(p.shape[0] * w for p, w in imgs)
     d_imgs = [(torch.from_numpy(np.ascontiguousarray(p)).to(dev), w) for p, w in imgs]
     max_side = max(max(p.shape[0], w) for p, w in imgs)
@@ -437,6 +439,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--subset", type=int, default=0, help="use only the first k images of the workload")
     ap.add_argument("--tight", action="store_true", help="node arrays sized w*h/4 instead of the bound")
+    ap.add_argument("--pick", default="", help="comma-separated image indices of the workload to use")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()

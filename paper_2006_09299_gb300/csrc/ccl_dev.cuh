@@ -26,7 +26,9 @@ constexpr int TW = 1024;               // tile width in pixels (32 words)
 constexpr int WPR = TW / 32;           // 32-bit words per tile row = lanes
 constexpr int TH = 32;                 // tile height in rows
 constexpr int TILE_PX = TH * TW;       // 32768: local pixel index fits 15 bits
-constexpr int NTHREADS = 256;          // threads of the tile kernels
+constexpr int NTHREADS = 256;          // threads of the write / resolve / canon kernels
+constexpr int LABEL_THREADS = 512;     // threads of the labelling kernel: two rows per warp
+constexpr int LABEL_WARPS = LABEL_THREADS / 32;
 constexpr int NWARPS = NTHREADS / 32;
 constexpr int MAXR = 4096;             // local roots with on-chip feature records
 constexpr int SCAN_B = 256;            // segments per block of the node scan
@@ -211,23 +213,21 @@ __device__ __forceinline__ int image_of_tile(const Batch &B, int t) {
 }
 
 // --------------------------------------------- in-tile union-find (shared)
-// Parents are 16-bit run-start indices; a root is its own parent and every
-// link points to a smaller index. Minimum-linking uses a CAS loop because
-// there is no 16-bit atomic minimum.
+// Parents are 32-bit run-start indices (row * TW + column); a root is its
+// own parent and every link points to a smaller index, so a native shared
+// atomicMin both links and resolves races: the union by minimum of
+// Algorithm 2 on the tile's label space.
 
-__device__ __forceinline__ unsigned short atomic_min_u16(unsigned short *p, unsigned short v) {
-    unsigned short old = *(volatile unsigned short *)p;
-    while (old > v) {
-        unsigned short prev = atomicCAS(p, old, v);
-        if (prev == old) return old;
-        old = prev;
-    }
-    return old;
-}
+// Shared-memory slot of entry i of a per-pixel or per-run table. Entries
+// are addressed as row * 1024 + 32 * lane + bit (or lane * runs-per-word +
+// j), so the lanes of a warp touch the same bit position of their words at
+// the same time; XOR-ing the low five bits with the next five spreads them
+// over the 32 banks. The map is a bijection on every block of 1024 entries.
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 5) & 31); }
 
-__device__ __forceinline__ int local_find(unsigned short *par, int a, bool *ok) {
+__device__ __forceinline__ int local_find(const uint32_t *par, int a, bool *ok) {
     for (int it = 0; it < LOCAL_FIND_LIMIT; ++it) {
-        int p = *(volatile unsigned short *)(par + a);
+        const int p = (int)*(volatile const uint32_t *)(par + swz(a));
         if (p == a) return a;
         a = p;
     }
@@ -235,13 +235,13 @@ __device__ __forceinline__ int local_find(unsigned short *par, int a, bool *ok) 
     return a;
 }
 
-__device__ __forceinline__ void local_union(unsigned short *par, int a, int b, bool *ok) {
+__device__ __forceinline__ void local_union(uint32_t *par, int a, int b, bool *ok) {
     for (int it = 0; it < LOCAL_UNION_LIMIT; ++it) {
         a = local_find(par, a, ok);
         b = local_find(par, b, ok);
         if (a == b || !*ok) return;
-        if (a < b) { int t = a; a = b; b = t; }
-        unsigned short old = atomic_min_u16(par + a, (unsigned short)b);
+        if (a < b) { const int t = a; a = b; b = t; }
+        const int old = (int)atomicMin(par + swz(a), (uint32_t)b);
         if (old == a) return;
         a = old;
     }
@@ -310,22 +310,24 @@ __device__ __forceinline__ void feat_atomic(int64_t *base, int64_t cap, int id, 
 // contributions a CTA makes to the same node before they reach global
 // memory: a component spanning many tiles (or a survivor absorbing many
 // holes) would otherwise receive one atomic per contribution on the same
-// address. Entries that do not fit go straight to global atomics.
+// address. Keys are (image << 32 | node); entries that do not fit go
+// straight to global atomics.
 constexpr int HT = 256;
-constexpr size_t HT_BYTES = (size_t)HT * (3 * 8 + 5 * 4);
+constexpr size_t HT_BYTES = (size_t)HT * (4 * 8 + 4 * 4);
+constexpr unsigned long long HT_EMPTY = ~0ull;
 
 struct HashTab {
-    unsigned long long *area, *sx, *sy;
-    int *key, *xmin, *ymin, *xmax, *ymax;
+    unsigned long long *key, *area, *sx, *sy;
+    int *xmin, *ymin, *xmax, *ymax;
 };
 
 __device__ __forceinline__ HashTab hash_carve(void *mem) {
     HashTab H;
-    H.area = (unsigned long long *)mem;
+    H.key = (unsigned long long *)mem;
+    H.area = H.key + HT;
     H.sx = H.area + HT;
     H.sy = H.sx + HT;
-    H.key = (int *)(H.sy + HT);
-    H.xmin = H.key + HT;
+    H.xmin = (int *)(H.sy + HT);
     H.ymin = H.xmin + HT;
     H.xmax = H.ymin + HT;
     H.ymax = H.xmax + HT;
@@ -334,7 +336,7 @@ __device__ __forceinline__ HashTab hash_carve(void *mem) {
 
 __device__ __forceinline__ void hash_init(const HashTab &H) {
     for (int e = threadIdx.x; e < HT; e += blockDim.x) {
-        H.key[e] = -1;
+        H.key[e] = HT_EMPTY;
         H.area[e] = 0;
         H.sx[e] = 0;
         H.sy[e] = 0;
@@ -345,31 +347,53 @@ __device__ __forceinline__ void hash_init(const HashTab &H) {
     }
 }
 
-__device__ __forceinline__ void hash_push(const HashTab &H, int64_t *base, int64_t cap, int id,
-                                          unsigned long long area, unsigned long long sx, unsigned long long sy,
-                                          int xmin, int ymin, int xmax, int ymax) {
-    const uint32_t h = ((uint32_t)id * 2654435761u) >> 24;
+// Features of one contribution (global coordinates).
+struct FeatAcc {
+    unsigned long long area, sx, sy;
+    int xmin, ymin, xmax, ymax;
+};
+
+__device__ __forceinline__ void acc_merge(FeatAcc &a, const FeatAcc &b) {
+    a.area += b.area;
+    a.sx += b.sx;
+    a.sy += b.sy;
+    a.xmin = min(a.xmin, b.xmin);
+    a.ymin = min(a.ymin, b.ymin);
+    a.xmax = max(a.xmax, b.xmax);
+    a.ymax = max(a.ymax, b.ymax);
+}
+
+// base / cap: the feature table the entry belongs to (used when the table is full).
+__device__ __forceinline__ void hash_push(const HashTab &H, int64_t *base, int64_t cap, int img, int id,
+                                          const FeatAcc &v) {
+    const unsigned long long key = ((unsigned long long)(uint32_t)img << 32) | (uint32_t)id;
+    const uint32_t h = ((uint32_t)id * 2654435761u + (uint32_t)img * 40503u) >> 24;
     for (int probe = 0; probe < 8; ++probe) {
         const int e = (h + probe) & (HT - 1);
-        const int prev = atomicCAS(H.key + e, -1, id);
-        if (prev == -1 || prev == id) {
-            atomicAdd(H.area + e, area);
-            atomicAdd(H.sx + e, sx);
-            atomicAdd(H.sy + e, sy);
-            atomicMin(H.xmin + e, xmin);
-            atomicMin(H.ymin + e, ymin);
-            atomicMax(H.xmax + e, xmax);
-            atomicMax(H.ymax + e, ymax);
+        const unsigned long long prev = atomicCAS(H.key + e, HT_EMPTY, key);
+        if (prev == HT_EMPTY || prev == key) {
+            atomicAdd(H.area + e, v.area);
+            atomicAdd(H.sx + e, v.sx);
+            atomicAdd(H.sy + e, v.sy);
+            atomicMin(H.xmin + e, v.xmin);
+            atomicMin(H.ymin + e, v.ymin);
+            atomicMax(H.xmax + e, v.xmax);
+            atomicMax(H.ymax + e, v.ymax);
             return;
         }
     }
-    feat_atomic(base, cap, id, area, sx, sy, xmin, ymin, xmax, ymax);
+    feat_atomic(base, cap, id, v.area, v.sx, v.sy, v.xmin, v.ymin, v.xmax, v.ymax);
 }
 
-__device__ __forceinline__ void hash_flush(const HashTab &H, int64_t *base, int64_t cap) {
+// Flush every entry into the feature table of its image: the analysed
+// features (filled = false) or the filled ones.
+__device__ __forceinline__ void hash_flush(const HashTab &H, const ImgDesc *desc, bool filled) {
     for (int e = threadIdx.x; e < HT; e += blockDim.x) {
-        const int id = H.key[e];
-        if (id >= 0) feat_atomic(base, cap, id, H.area[e], H.sx[e], H.sy[e], H.xmin[e], H.ymin[e], H.xmax[e], H.ymax[e]);
+        const unsigned long long key = H.key[e];
+        if (key == HT_EMPTY) continue;
+        const ImgDesc &d = desc[key >> 32];
+        feat_atomic(filled ? d.filled_feat : d.feat, d.cap, (int)(uint32_t)key, H.area[e], H.sx[e], H.sy[e],
+                    H.xmin[e], H.ymin[e], H.xmax[e], H.ymax[e]);
     }
 }
 

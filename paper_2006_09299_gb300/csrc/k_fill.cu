@@ -10,6 +10,11 @@
 //
 //   k_fill_map    map, survivor features copied, parents of survivors
 //   k_fill_merge  features of absorbed nodes merged into their survivor
+//
+// Both kernels walk one flat index over the nodes of every image of the last
+// analysis: image i's nodes start at i + seg_base[first segment of i], since
+// the node scan runs across all images in order and each image adds its
+// exterior node.
 #include "ccl_dev.cuh"
 
 namespace ccl {
@@ -55,24 +60,43 @@ __device__ __forceinline__ int survivor(const FillView &v, int m, bool *ok) {
     return m;
 }
 
-__device__ __forceinline__ int fill_nodes(const ImgDesc &d) {
-    const int n = d.counts[0];
-    return (int)min((int64_t)n, min(d.cap, d.ncap));
+__device__ __forceinline__ int64_t node_base(const Batch &B, int i) {
+    return (int64_t)i + B.s.seg_base[B.desc[i].seg0];
 }
 
+// Image of flat node index f (cached range [lo, hi) of image img).
+struct ImageCursor {
+    int img = -1;
+    int64_t lo = 0, hi = 0;
+    __device__ void seek(const Batch &B, int64_t f) {
+        if (f >= lo && f < hi) return;
+        int a = 0, b = B.n_img - 1;
+        while (a < b) {
+            const int mid = (a + b + 1) >> 1;
+            if (node_base(B, mid) <= f) a = mid; else b = mid - 1;
+        }
+        img = a;
+        lo = node_base(B, a);
+        hi = a + 1 < B.n_img ? node_base(B, a + 1) : (int64_t)B.n_img + B.s.seg_base[B.n_segs];
+    }
+};
+
 __global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T) {
-    const ImgDesc &d = B.desc[blockIdx.y];
-    if (d.fill_map == nullptr) return;
-    const int n = fill_nodes(d);
-    const FillView v{d.parent, d.feat, B.s.node_fg + d.node0, T};
-    const int64_t cap = d.cap;
-    bool ok = true;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int64_t total = (int64_t)B.n_img + B.s.seg_base[B.n_segs];
+    ImageCursor cur;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+        cur.seek(B, f);
+        const ImgDesc &d = B.desc[cur.img];
+        const int k = (int)(f - cur.lo);
+        if (d.fill_map == nullptr || k >= min(d.cap, d.ncap)) continue;
+        const FillView v{d.parent, d.feat, B.s.node_fg + d.node0, T};
+        const int64_t cap = d.cap;
+        bool ok = true;
         const int s = survivor(v, k, &ok);
         d.fill_map[k] = s;
         if (s == k) {
 #pragma unroll
-            for (int f = 0; f < 7; ++f) d.filled_feat[f * cap + k] = d.feat[f * cap + k];
+            for (int q = 0; q < 7; ++q) d.filled_feat[q * cap + k] = d.feat[q * cap + k];
             const int p = d.parent[k];
             d.filled_parent[k] = p < 0 ? -1 : survivor(v, p, &ok);
         } else {
@@ -85,34 +109,56 @@ __global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T) {
             d.filled_feat[6 * cap + k] = 0;
             d.filled_parent[k] = -1;
         }
+        if (!ok) set_status(B, d, ST_ITER);
     }
-    if (!ok) set_status(B, d, ST_ITER);
 }
 
+// Absorbed nodes add their features to their survivor. Each thread first
+// sums consecutive contributions to the same survivor in registers (a
+// survivor absorbing many holes is met again and again by the same thread),
+// then goes through the CTA's hash table, then global atomics.
 __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
     __shared__ __align__(16) unsigned char hmem[HT_BYTES];
-    const ImgDesc &d = B.desc[blockIdx.y];
-    if (d.fill_map == nullptr) return;
-    const int n = fill_nodes(d);
-    const int64_t cap = d.cap;
     const HashTab H = hash_carve(hmem);
     hash_init(H);
     __syncthreads();
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int64_t total = (int64_t)B.n_img + B.s.seg_base[B.n_segs];
+    ImageCursor cur;
+    int acc_img = -1, acc_id = -1;
+    FeatAcc acc{};
+    auto flush = [&]() {
+        if (acc_id >= 0) {
+            const ImgDesc &d = B.desc[acc_img];
+            hash_push(H, d.filled_feat, d.cap, acc_img, acc_id, acc);
+        }
+    };
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
+        cur.seek(B, f);
+        const ImgDesc &d = B.desc[cur.img];
+        const int k = (int)(f - cur.lo);
+        if (d.fill_map == nullptr || k >= min(d.cap, d.ncap)) continue;
         const int s = d.fill_map[k];
         if (s == k) continue;
-        hash_push(H, d.filled_feat, cap, s, (unsigned long long)d.feat[0 * cap + k],
-                  (unsigned long long)d.feat[5 * cap + k], (unsigned long long)d.feat[6 * cap + k],
-                  (int)d.feat[1 * cap + k], (int)d.feat[2 * cap + k], (int)d.feat[3 * cap + k],
-                  (int)d.feat[4 * cap + k]);
+        const int64_t cap = d.cap;
+        const FeatAcc v{(unsigned long long)d.feat[0 * cap + k], (unsigned long long)d.feat[5 * cap + k],
+                        (unsigned long long)d.feat[6 * cap + k], (int)d.feat[1 * cap + k],
+                        (int)d.feat[2 * cap + k], (int)d.feat[3 * cap + k], (int)d.feat[4 * cap + k]};
+        if (s == acc_id && cur.img == acc_img) {
+            acc_merge(acc, v);
+        } else {
+            flush();
+            acc_img = cur.img;
+            acc_id = s;
+            acc = v;
+        }
     }
+    flush();
     __syncthreads();
-    hash_flush(H, d.filled_feat, cap);
+    hash_flush(H, B.desc, true);
 }
 
 void launch_fill(const Batch &B, int64_t T, const LaunchCfg &c, cudaStream_t st, const cudaEvent_t *ev) {
-    const int bx = max(1, (4 * c.sms + B.n_img - 1) / B.n_img);
-    const dim3 grid(bx, B.n_img);
+    const int grid = 8 * c.sms;
     if (ev) cudaEventRecord(ev[0], st);
     k_fill_map<<<grid, 256, 0, st>>>(B, T);
     if (ev) cudaEventRecord(ev[1], st);

@@ -61,11 +61,70 @@ __device__ __forceinline__ int run_start_col(const uint32_t (*sE)[WPR], const ui
     return m ? (l << 5) + 31 - __clz(m) : (int)sRS[r][l];
 }
 
+// Union every run of row r with the runs of row r - 1 it touches, lane =
+// 32-pixel word. Masks mark, once per pair of touching runs, the column
+// where the pair is tested:
+//   va / vb  vertical overlaps of the 8- / 4-adjacent colour, at the first
+//            column of the overlap (where one of the two runs starts);
+//   d1 / d2  diagonal-only contacts of the 8-adjacent colour, up-right and
+//            up-left (Algorithm 2 widens the 8-adjacent run's window by one
+//            pixel on each side).
 template <int CONN>
-__global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
+__device__ __forceinline__ void unify_rows(uint32_t *par, const uint32_t (*sC)[WPR],
+                                           const uint32_t (*sE)[WPR], const uint16_t (*sRS)[WPR], int r,
+                                           int lane, uint32_t vm, bool *ok) {
+    const uint32_t cc = sC[r][lane], cu = sC[r - 1][lane];
+    const uint32_t ec = sE[r][lane], eu = sE[r - 1][lane];
+    const uint32_t ac = CONN ? (~cc & vm) : cc;   // the 8-adjacent colour
+    const uint32_t au = CONN ? (~cu & vm) : cu;
+    const uint32_t bc = CONN ? cc : (~cc & vm);   // the 4-adjacent colour
+    const uint32_t bu = CONN ? cu : (~cu & vm);
+    uint32_t acl = __shfl_up_sync(FULL, ac, 1), acr = __shfl_down_sync(FULL, ac, 1);
+    uint32_t aul = __shfl_up_sync(FULL, au, 1), aur = __shfl_down_sync(FULL, au, 1);
+    if (lane == 0) acl = aul = 0;
+    if (lane == 31) acr = aur = 0;
+    const uint32_t ac_prev = (ac << 1) | (acl >> 31);   // bit x: pixel x-1
+    const uint32_t ac_next = (ac >> 1) | (acr << 31);   // bit x: pixel x+1
+    const uint32_t au_prev = (au << 1) | (aul >> 31);
+    const uint32_t au_next = (au >> 1) | (aur << 31);
+    const uint32_t va = ac & au & ((ec & ac) | (eu & au));
+    const uint32_t vb = bc & bu & ((ec & bc) | (eu & bu));
+    const uint32_t d1 = ac & ~au & au_next & ~ac_next;   // (r,x)-(r-1,x+1)
+    const uint32_t d2 = ac & ~au & au_prev & ~ac_prev;   // (r,x)-(r-1,x-1)
+    // (a pixel can have both diagonal contacts: d2 gets its own pass)
+    uint32_t m = va | vb | d1;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int x = 32 * lane + b;
+        const int xu = ((d1 >> b) & 1u) ? x + 1 : x;
+        local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, xu), ok);
+    }
+    m = d2;
+    while (m) {
+        const int x = 32 * lane + __ffs(m) - 1;
+        m &= m - 1;
+        local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, x - 1), ok);
+    }
+}
+
+// Point every run of row r at its current root.
+__device__ __forceinline__ void compress_row(uint32_t *par, const uint32_t (*sE)[WPR], int r, int lane,
+                                             bool *ok) {
+    uint32_t m = sE[r][lane];
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int idx = r * TW + 32 * lane + b;
+        par[swz(idx)] = (uint32_t)local_find(par, idx, ok);
+    }
+}
+
+template <int CONN>
+__global__ void __launch_bounds__(LABEL_THREADS, 1) k_label(Batch B) {
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned short *par = (unsigned short *)smem;                        // 64 KB
-    uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(smem + TILE_PX * 2);         // colour bits
+    uint32_t *par = (uint32_t *)smem;                                    // 128 KB
+    uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(smem + TILE_PX * 4);         // colour bits
     uint32_t(*sE)[WPR] = sC + TH;                                        // run starts
     uint32_t(*sR)[WPR] = sE + TH;                                        // local roots
     uint32_t(*sB)[WPR] = sR + TH;                                        // border roots
@@ -99,7 +158,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
         bool ok = true;
 
         // ---- read the tile, pack bits, find run starts
-        for (int r = warp; r < TH; r += NWARPS) {
+        for (int r = warp; r < TH; r += LABEL_WARPS) {
             uint32_t word = 0;
             if (r < th && vcnt > 0) {
                 const uint8_t *p = d.img + (int64_t)(y0 + r) * d.pitch + x0 + 32 * lane;
@@ -128,60 +187,32 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
                 const int idx = r * TW + 32 * lane + b;
-                par[idx] = (unsigned short)idx;
+                par[swz(idx)] = (uint32_t)idx;
             }
         }
         __syncthreads();
 
-        // ---- unify each row with the row above (Algorithm 2, all rows at once)
-        for (int r = 1 + warp; r < th; r += NWARPS) {
-            const uint32_t cc = sC[r][lane], cu = sC[r - 1][lane];
-            const uint32_t ec = sE[r][lane], eu = sE[r - 1][lane];
-            const uint32_t ac = CONN ? (~cc & vm) : cc;   // the 8-adjacent colour
-            const uint32_t au = CONN ? (~cu & vm) : cu;
-            const uint32_t bc = CONN ? cc : (~cc & vm);   // the 4-adjacent colour
-            const uint32_t bu = CONN ? cu : (~cu & vm);
-            uint32_t acl = __shfl_up_sync(FULL, ac, 1), acr = __shfl_down_sync(FULL, ac, 1);
-            uint32_t aul = __shfl_up_sync(FULL, au, 1), aur = __shfl_down_sync(FULL, au, 1);
-            if (lane == 0) acl = aul = 0;
-            if (lane == 31) acr = aur = 0;
-            const uint32_t ac_prev = (ac << 1) | (acl >> 31);   // bit x: pixel x-1
-            const uint32_t ac_next = (ac >> 1) | (acr << 31);   // bit x: pixel x+1
-            const uint32_t au_prev = (au << 1) | (aul >> 31);
-            const uint32_t au_next = (au >> 1) | (aur << 31);
-            // vertical overlaps, tested once per pair of runs at the first
-            // column of the overlap, where one of the two runs starts
-            const uint32_t va = ac & au & ((ec & ac) | (eu & au));
-            const uint32_t vb = bc & bu & ((ec & bc) | (eu & bu));
-            // diagonal-only contacts of the 8-adjacent colour
-            const uint32_t d1 = ac & ~au & au_next & ~ac_next;   // (r,x)-(r-1,x+1)
-            const uint32_t d2 = ac & ~au & au_prev & ~ac_prev;   // (r,x)-(r-1,x-1)
-            uint32_t m = va | vb;
-            while (m) {
-                const int x = 32 * lane + __ffs(m) - 1;
-                m &= m - 1;
-                local_union(par, r * TW + run_start_col(sE, sRS, r, x),
-                            (r - 1) * TW + run_start_col(sE, sRS, r - 1, x), &ok);
-            }
-            m = d1;
-            while (m) {
-                const int x = 32 * lane + __ffs(m) - 1;
-                m &= m - 1;
-                local_union(par, r * TW + run_start_col(sE, sRS, r, x),
-                            (r - 1) * TW + run_start_col(sE, sRS, r - 1, x + 1), &ok);
-            }
-            m = d2;
-            while (m) {
-                const int x = 32 * lane + __ffs(m) - 1;
-                m &= m - 1;
-                local_union(par, r * TW + run_start_col(sE, sRS, r, x),
-                            (r - 1) * TW + run_start_col(sE, sRS, r - 1, x - 1), &ok);
-            }
+        // ---- unify each row with the row above (Algorithm 2)
+        // Warp w first unifies its own row pair (2w, 2w + 1) and points row
+        // 2w + 1 at the new roots, like one step of the paper's row-by-row
+        // scan. Then blocks of 4, 8, 16 and 32 rows are joined across their
+        // middle row, one boundary per warp and one level at a time, so that
+        // every tree stays a few links deep.
+        if (2 * warp + 1 < th) {
+            unify_rows<CONN>(par, sC, sE, sRS, 2 * warp + 1, lane, vm, &ok);
+            __syncwarp();
+            compress_row(par, sE, 2 * warp + 1, lane, &ok);
+        }
+#pragma unroll 1
+        for (int bs = 4; bs <= TH; bs *= 2) {
+            __syncthreads();
+            const int r = bs * warp + bs / 2;
+            if (warp < TH / bs && r < th) unify_rows<CONN>(par, sC, sE, sRS, r, lane, vm, &ok);
         }
         __syncthreads();
 
         // ---- closure: every run points at its root (Algorithm 3, in-tile)
-        for (int r = warp; r < TH; r += NWARPS) {
+        for (int r = warp; r < TH; r += LABEL_WARPS) {
             uint32_t roots = 0;
             uint32_t m = r < th ? sE[r][lane] : 0u;
             while (m) {
@@ -189,7 +220,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
                 m &= m - 1;
                 const int idx = r * TW + 32 * lane + b;
                 const int root = local_find(par, idx, &ok);
-                par[idx] = (unsigned short)root;
+                par[swz(idx)] = (uint32_t)root;
                 if (root == idx) roots |= 1u << b;
             }
             sR[r][lane] = roots;
@@ -199,19 +230,19 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
 
         // ---- roots of the edge cells are border roots
         const int nedge = 2 * tw + 2 * th;
-        for (int i = threadIdx.x; i < nedge; i += NTHREADS) {
+        for (int i = threadIdx.x; i < nedge; i += LABEL_THREADS) {
             int r, c;
             if (i < tw) { r = 0; c = i; }
             else if (i < 2 * tw) { r = th - 1; c = i - tw; }
             else if (i < 2 * tw + th) { r = i - 2 * tw; c = 0; }
             else { r = i - 2 * tw - th; c = tw - 1; }
-            const int root = par[r * TW + run_start_col(sE, sRS, r, c)];
+            const int root = par[swz(r * TW + run_start_col(sE, sRS, r, c))];
             atomicOr(&sB[root >> 10][(root >> 5) & 31], 1u << (root & 31));
         }
         __syncthreads();
 
         // ---- ordinals of roots and border roots in raster order
-        for (int r = warp; r < TH; r += NWARPS) {
+        for (int r = warp; r < TH; r += LABEL_WARPS) {
             int tr, tb;
             const int pr = warp_excl_sum(__popc(sR[r][lane]), &tr);
             const int pb = warp_excl_sum(__popc(sB[r][lane]), &tb);
@@ -240,14 +271,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
         uint32_t *ri = B.s.rootinfo + g.px;
         const uint32_t slot0 = (uint32_t)(B.n_img + g.b);
         int nfg = 0;
-        for (int r = warp; r < th; r += NWARPS) {
+        for (int r = warp; r < th; r += LABEL_WARPS) {
             const uint32_t e = sE[r][lane], rm = sR[r][lane], bm = sB[r][lane], c = sC[r][lane];
             int q = sRowTot[0][r] + sRunPre[r][lane];
             uint32_t m = e;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
-                const int root = par[r * TW + 32 * lane + b];
+                const int root = par[swz(r * TW + 32 * lane + b)];
                 const int rrow = root >> 10, rl = (root >> 5) & 31;
                 const int k = sRowTot[1][rrow] + sRootPre[rrow][rl] +
                               __popc(sR[rrow][rl] & mask_lt(root & 31));
@@ -278,14 +309,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
         // edge cells -> border ordinal of their root
         // (cell i of the loop is also its offset: top, bottom, left, right)
         uint16_t *eg = B.s.edges + g.b;
-        for (int i = threadIdx.x; i < nedge; i += NTHREADS) {
+        for (int i = threadIdx.x; i < nedge; i += LABEL_THREADS) {
             int r, c;
             if (i < tw) { r = 0; c = i; }
             else if (i < 2 * tw) { r = th - 1; c = i - tw; }
             else if (i < 2 * tw + th) { r = i - 2 * tw; c = 0; }
             else { r = i - 2 * tw - th; c = tw - 1; }
             const int off = i;
-            const int root = par[r * TW + run_start_col(sE, sRS, r, c)];
+            const int root = par[swz(r * TW + run_start_col(sE, sRS, r, c))];
             const int rrow = root >> 10, rl = (root >> 5) & 31;
             eg[off] = (uint16_t)(sRowTot[2][rrow] + sBPre[rrow][rl] + __popc(sB[rrow][rl] & mask_lt(root & 31)));
         }
@@ -301,18 +332,18 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_label(Batch B) {
     }
 }
 
-constexpr size_t LABEL_SMEM = TILE_PX * 2 + 4 * TH * WPR * 4 + 4 * TH * WPR * 2;
+constexpr size_t LABEL_SMEM = TILE_PX * 4 + 4 * TH * WPR * 4 + 4 * TH * WPR * 2;
 
 void launch_prologue(const Batch &B, cudaStream_t st) {
     k_prologue<<<(B.n_img + 127) / 128, 128, 0, st>>>(B);
 }
 
 void launch_label(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    const int grid = min(B.n_tiles, 2 * c.sms);
+    const int grid = min(B.n_tiles, c.sms);
     if (B.conn == 0)
-        k_label<0><<<grid, NTHREADS, LABEL_SMEM, st>>>(B);
+        k_label<0><<<grid, LABEL_THREADS, LABEL_SMEM, st>>>(B);
     else
-        k_label<1><<<grid, NTHREADS, LABEL_SMEM, st>>>(B);
+        k_label<1><<<grid, LABEL_THREADS, LABEL_SMEM, st>>>(B);
 }
 
 cudaError_t configure_label() {

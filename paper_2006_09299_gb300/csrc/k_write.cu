@@ -40,6 +40,25 @@ __device__ __forceinline__ bool box_update(uint32_t *p, int xs, int xl, int r) {
     return false;
 }
 
+// Features of consecutive runs of one root on one row (tile-local x).
+struct RunAcc {
+    int k = -1;
+    uint32_t len = 0, sx = 0;
+    int x0 = 0, x1 = 0;
+    __device__ __forceinline__ void start(int kk, int xs, int xe) {
+        k = kk;
+        len = (uint32_t)(xe - xs);
+        sx = (uint32_t)((xs + xe - 1) * (xe - xs) / 2);
+        x0 = xs;
+        x1 = xe - 1;
+    }
+    __device__ __forceinline__ void add(int xs, int xe) {
+        len += (uint32_t)(xe - xs);
+        sx += (uint32_t)((xs + xe - 1) * (xe - xs) / 2);
+        x1 = xe - 1;
+    }
+};
+
 __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e) {
     asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e) : "memory");
 }
@@ -88,7 +107,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
         const uint32_t slot0 = (uint32_t)(n_img + g.b);
         const int vcnt = min(max(tw - 32 * lane, 0), 32);
         const uint32_t vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
-        bool ok = true;
+        bool ok = true, over = false;
 
         // ---- bit planes of the tile: colour, run starts, node first-pixels
         for (int r = warp; r < TH; r += NWARPS) {
@@ -150,36 +169,78 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
         }
         __syncthreads();
 
-        // ---- rows: run features, then the label rows
+        // ---- rows: run features, tree parents of the row below, label rows
         const bool labels = B.labels && d.fg != nullptr;
         for (int r = warp; r < th; r += NWARPS) {
             const uint32_t e = sE[r][lane];
             const int rowbase = sRowRun[r];
-            int q = rowbase + sRunPre[r][lane];
-            const int first = e ? 32 * lane + __ffs(e) - 1 : TW;
-            const int nxt = min(warp_suffix_min_excl(first, TW), tw);
+            const int nr = (r + 1 < TH ? sRowRun[r + 1] : st.x) - rowbase;
             int32_t *rid = sRid + warp * TW;
-            uint32_t m = e;
-            while (m) {
-                const int xs = 32 * lane + __ffs(m) - 1;
-                m &= m - 1;
-                const int xe = m ? 32 * lane + __ffs(m) - 1 : nxt;
-                const int k = rr[q];
-                const int id = k < MAXR ? sId[k] : root_id(ri[k]);
-                rid[q - rowbase] = id;
-                ++q;
-                const int len = xe - xs;
-                const unsigned long long sxl = (unsigned long long)((xs + xe - 1) * len / 2);
-                if (k < MAXR) {
-                    atomicAdd(&sSum[k], (unsigned long long)len | (sxl << 16) |
-                                            ((unsigned long long)(r * len) << 41));
-                    ok &= box_update(&sBox[k], xs, xe - 1, r);
-                } else if (id < cap) {
-                    feat_atomic(d.feat, cap, id, len, sxl + (unsigned long long)x0 * len,
-                                (unsigned long long)(y0 + r) * len, x0 + xs, y0 + r, x0 + xe - 1, y0 + r);
+            // root ordinals of the row's runs: one coalesced pass
+#pragma unroll 4
+            for (int i = lane; i < nr; i += 32) rid[swz(i)] = rr[rowbase + i];
+            __syncwarp();
+            // each lane walks the runs starting in its word. Along a row the
+            // runs alternate colours, so a component crossing the row many
+            // times (the percolating one of a dense random image) owns every
+            // other run: one register accumulator per run parity sums its
+            // runs, and the shared record is updated only when the root changes.
+            {
+                const int first = e ? 32 * lane + __ffs(e) - 1 : TW;
+                const int nxt = min(warp_suffix_min_excl(first, TW), tw);
+                int q = sRunPre[r][lane];
+                uint32_t m = e;
+                RunAcc acc0, acc1;
+                auto flush = [&](const RunAcc &a) {
+                    if (a.k < 0) return;
+                    if (a.k < MAXR) {
+                        atomicAdd(&sSum[a.k], (unsigned long long)a.len | ((unsigned long long)a.sx << 16) |
+                                                  ((unsigned long long)(r * a.len) << 41));
+                        ok &= box_update(&sBox[a.k], a.x0, a.x1, r);
+                    } else {
+                        const int id = root_id(ri[a.k]);
+                        if (id < cap)
+                            feat_atomic(d.feat, cap, id, a.len, a.sx + (unsigned long long)x0 * a.len,
+                                        (unsigned long long)(y0 + r) * a.len, x0 + a.x0, y0 + r, x0 + a.x1, y0 + r);
+                    }
+                };
+                while (m) {
+                    const int xs = 32 * lane + __ffs(m) - 1;
+                    m &= m - 1;
+                    const int xe = m ? 32 * lane + __ffs(m) - 1 : nxt;
+                    const int k = rid[swz(q)];
+                    rid[swz(q)] = k < MAXR ? sId[k] : root_id(ri[k]);
+                    RunAcc &acc = (q & 1) ? acc1 : acc0;
+                    if (k == acc.k) {
+                        acc.add(xs, xe);
+                    } else {
+                        flush(acc);
+                        acc.start(k, xs, xe);
+                    }
+                    ++q;
                 }
+                flush(acc0);
+                flush(acc1);
             }
             __syncwarp();
+            // nodes whose first pixel is on row r + 1: parent = node of the
+            // pixel above (the initial adjacency of Algorithm 2)
+            if (r + 1 < th) {
+                const uint32_t nb = sNB[r + 1][lane];
+                uint32_t m = nb;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int id = 1 + sRowSeg[r + 1] + sNBPre[r + 1][lane] + __popc(nb & mask_lt(b));
+                    const int p = rid[swz(sRunPre[r][lane] + __popc(e & mask_le(b)) - 1)];
+                    if (id < cap) {
+                        d.parent[id] = p;
+                        if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[r + 1][lane] >> b) & 1u);
+                    } else {
+                        over = true;
+                    }
+                }
+            }
             if (labels) {
                 int32_t *fgrow = d.fg + (int64_t)(y0 + r) * d.w + x0;
                 int32_t *bgrow = d.bg + (int64_t)(y0 + r) * d.w + x0;
@@ -194,7 +255,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int bit = b + j;
-                            const int id = rid[p + __popc(ew & mask_le(bit))];
+                            const int id = rid[swz(p + __popc(ew & mask_le(bit)))];
                             const bool isfg = (cw >> bit) & 1u;
                             fv[j] = isfg ? id : -1;
                             bv[j] = isfg ? -1 : id;
@@ -216,71 +277,67 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
             }
             __syncwarp();
         }
-        __syncthreads();
-
-        // ---- per local root: features and tree parent
-        hash_init(H);
-        __syncthreads();
-        bool over = false;
-        for (int k = threadIdx.x; k < n_roots; k += NTHREADS) {
-            const uint32_t info = ri[k];
-            const int idx = info & 0xFFFF, r = idx >> 10, c = idx & 1023;
-            const bool isb = (info >> 17) & 1u;
-            const int id = k < MAXR ? sId[k] : root_id(info);
-            bool isnode = !isb;
-            if (isb) {
-                const uint32_t slot = slot0 + (info >> 18);
-                isnode = (uint32_t)B.s.gp[slot] == slot;
-            }
-            if (k < MAXR) {
-                const unsigned long long s = sSum[k];
-                const uint32_t bx = sBox[k];
-                const long long area = (long long)(s & 0xFFFFull);
-                const long long sx = (long long)((s >> 16) & ((1ull << 25) - 1)) + area * x0;
-                const long long sy = (long long)((s >> 41) & ((1ull << 20) - 1)) + area * y0;
-                const int xmin = x0 + (int)(bx & 1023u), xmax = x0 + (int)((bx >> 10) & 1023u);
-                const int ymax = y0 + (int)(bx >> 20), ymin = y0 + r;
-                if (!isb) {
-                    if (id < cap) {
-                        d.feat[0 * cap + id] = area;
-                        d.feat[1 * cap + id] = xmin;
-                        d.feat[2 * cap + id] = ymin;
-                        d.feat[3 * cap + id] = xmax;
-                        d.feat[4 * cap + id] = ymax;
-                        d.feat[5 * cap + id] = sx;
-                        d.feat[6 * cap + id] = sy;
-                    }
-                } else if (id < cap) {
-                    hash_push(H, d.feat, cap, id, area, sx, sy, xmin, ymin, xmax, ymax);
-                }
-            }
-            if (isnode) {
-                if (id >= cap) {
-                    over = true;
-                    continue;
-                }
-                int p;
-                if (y0 + r == 0) {
-                    p = 0;
-                } else if (r > 0) {
-                    const int l = c >> 5;
-                    const int q = sRowRun[r - 1] + sRunPre[r - 1][l] + __popc(sE[r - 1][l] & mask_le(c & 31)) - 1;
-                    const int kk = rr[q];
-                    p = kk < MAXR ? sId[kk] : root_id(ri[kk]);
-                } else {
-                    const TileGeo ga = tile_geo(d, lt - d.TX);   // the tile above
+        // nodes whose first pixel is on the tile's top row: the pixel above is
+        // in the tile above (or outside the image: the exterior)
+        if (warp == NWARPS - 1) {
+            const uint32_t nb = sNB[0][lane];
+            uint32_t m = nb;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int c = 32 * lane + b;
+                const int id = 1 + sRowSeg[0] + sNBPre[0][lane] + __popc(nb & mask_lt(b));
+                int p = 0;
+                if (y0 > 0) {
+                    const TileGeo ga = tile_geo(d, lt - d.TX);
                     const uint32_t s2 = (uint32_t)(n_img + ga.b) + B.s.edges[ga.b + edge_bottom(ga, c)];
                     const uint32_t root = (uint32_t)B.s.gp[s2];
                     p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
                 }
-                d.parent[id] = p;
-                if (!isb && id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((info >> 16) & 1u);
+                if (id < cap) {
+                    d.parent[id] = p;
+                    if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[0][lane] >> b) & 1u);
+                } else {
+                    over = true;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- per local root: features
+        hash_init(H);
+        __syncthreads();
+        for (int k = threadIdx.x; k < min(n_roots, MAXR); k += NTHREADS) {
+            const uint32_t info = ri[k];
+            const int r = (info & 0xFFFF) >> 10;
+            const bool isb = (info >> 17) & 1u;
+            const int id = sId[k];
+            if (id >= cap) continue;
+            const unsigned long long s = sSum[k];
+            const uint32_t bx = sBox[k];
+            const long long area = (long long)(s & 0xFFFFull);
+            const long long sx = (long long)((s >> 16) & ((1ull << 25) - 1)) + area * x0;
+            const long long sy = (long long)((s >> 41) & ((1ull << 20) - 1)) + area * y0;
+            const int xmin = x0 + (int)(bx & 1023u), xmax = x0 + (int)((bx >> 10) & 1023u);
+            const int ymax = y0 + (int)(bx >> 20), ymin = y0 + r;
+            if (!isb) {
+                d.feat[0 * cap + id] = area;
+                d.feat[1 * cap + id] = xmin;
+                d.feat[2 * cap + id] = ymin;
+                d.feat[3 * cap + id] = xmax;
+                d.feat[4 * cap + id] = ymax;
+                d.feat[5 * cap + id] = sx;
+                d.feat[6 * cap + id] = sy;
+            } else {
+                const FeatAcc v{(unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
+                                xmin, ymin, xmax, ymax};
+                hash_push(H, d.feat, cap, sImg, id, v);
             }
         }
         if (!ok) atomicAnd(&sOk, 0);
         if (over) atomicOr(&sCap, 1);
         __syncthreads();
-        hash_flush(H, d.feat, cap);
+        hash_flush(H, B.desc, false);
         if (threadIdx.x == 0) {
             if (!sOk) set_status(B, d, ST_ITER);
             if (sCap) set_status(B, d, ST_CAPACITY);
