@@ -216,6 +216,38 @@ ccl_status ccl_read_phase_timing(ccl_ctx *ctx, double *total_ms, int64_t *count)
  * (graph replays count the kernels they contain). */
 ccl_status ccl_get_launch_count(ccl_ctx *ctx, int64_t *launches);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* ccl_analyze_static has no counterpart in the paper. It runs the same
+ * single-image analysis as ccl_create + ccl_analyze, but takes its scratch
+ * from a fixed array that the library keeps on every GPU that loads it
+ * (CCL_STATIC_SCRATCH_BYTES, held until the process exits) and allocates
+ * nothing. It is meant for callers that cannot call cudaMalloc: code whose
+ * device memory is owned entirely by another allocator, and latency-critical
+ * loops that must not allocate after start-up because cudaMalloc / cudaFree
+ * can synchronise the device and take unbounded time.
+ *
+ * Limits: w * h <= CCL_STATIC_MAX_PIXELS and w, h <= CCL_STATIC_MAX_SIDE;
+ * larger images return CCL_ERR_CAPACITY with nothing enqueued. Other
+ * arguments are as for ccl_analyze (8-foreground / 4-background adjacency),
+ * with capacity = length of d_tree_parent and row stride of d_features
+ * (ccl_node_capacity(w, h) always suffices; fewer slots are allowed and
+ * reported through d_counts[3] |= CCL_ERR_CAPACITY when exceeded).
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address and sets kernel attributes; make that first call
+ * before any stream capture. All calls share one array per device: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be ordered by the caller. Each call clears the counters it needs; the
+ * array keeps the last call's tables otherwise. */
+#define CCL_STATIC_MAX_PIXELS (1 << 20)
+#define CCL_STATIC_MAX_SIDE 4096
+#define CCL_STATIC_SCRATCH_BYTES (10 << 20)
+ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch,
+                              int32_t *d_fg_labels, int32_t *d_bg_labels, int32_t *d_tree_parent,
+                              int64_t *d_features, int64_t capacity, int32_t *d_counts,
+                              ccl_stream_t stream);
+
 const char *ccl_status_string(ccl_status status);
 
 /* Free the context and its scratch (waits for its pending work). */

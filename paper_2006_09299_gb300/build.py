@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libccl.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["k_label.cu", "k_merge.cu", "k_write.cu", "k_fill.cu", "ccl_api.cu"]
+SOURCES = ["k_label.cu", "k_merge.cu", "k_write.cu", "k_fill.cu", "ccl_api.cu", "ccl_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -51,6 +51,7 @@ SIGNATURES = {
     "ccl_enable_phase_timing": (ctypes.c_int, [_p, _i32]),
     "ccl_read_phase_timing": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "ccl_get_launch_count": (ctypes.c_int, [_p, ctypes.POINTER(_i64)]),
+    "ccl_analyze_static": (ctypes.c_int, [_p, _i32, _i32, _i32, _p, _p, _p, _p, _i64, _p, _p]),
     "ccl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ccl_destroy": (None, [_p]),
 }
@@ -239,3 +240,18 @@ class BatchContext(_Instrumented):
             self.close()
         except Exception:
             pass
+
+
+STATIC_MAX_PIXELS = 1 << 20
+STATIC_MAX_SIDE = 4096
+
+
+def analyze_static(img, w, out, stream=None):
+    """ccl_analyze_static: one analysis without any device allocation by the
+    library (scratch in a fixed per-device array; images up to
+    STATIC_MAX_PIXELS pixels). `out` is an Analysis with preallocated
+    tensors; img is a uint8 CUDA tensor [h][pitch]."""
+    _check(_lib.ccl_analyze_static(_ptr(img), int(w), int(img.shape[0]), int(img.stride(0)), _ptr(out.fg),
+                                   _ptr(out.bg), _ptr(out.parent), _ptr(out.features), int(out.cap),
+                                   _ptr(out.counts), _stream(stream)), "ccl_analyze_static")
+    return out

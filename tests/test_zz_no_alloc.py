@@ -1,0 +1,80 @@
+"""ccl_analyze_static: the analysis for callers that cannot allocate device
+memory (their memory belongs to another allocator, or they run loops that
+must not call cudaMalloc after start-up). Its scratch is a fixed per-device
+array inside the library; these tests check, through the C ABI, that two
+calls in a row give exactly what the allocating entry point gives, and that
+oversized images are refused before anything is enqueued.
+
+This file is collected last on purpose, so that a run stopping at the first
+failure has already run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2006_09299_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ccl():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2006_09299_gb300 import ccl as m
+    return m
+
+
+def reference_outputs(ccl, padded, w):
+    """The same image through ccl_create + ccl_analyze."""
+    h, pitch = padded.shape
+    ctx = ccl.Context(w, h, pitch)
+    out = ctx.analyze(torch.from_numpy(padded).cuda())
+    n, _, _, st = ctx.get_counts()
+    assert st == 0
+    res = (out.fg.cpu(), out.bg.cpu(), out.parent[:n].cpu(), out.features[:, :n].cpu(), out.counts[:3].cpu())
+    ctx.close()
+    return res
+
+
+def test_static_matches_allocating_entry_point_twice(ccl):
+    cases = [(inputs.granular(700, 1400, 0.5, 1, 11), 1400, 1408),
+             (inputs.granular(513, 2000, 0.35, 3, 12), 2000, 2000)]
+    for padded_img, w, pitch in cases:
+        padded = inputs.pitched(padded_img, pitch)
+        ref = reference_outputs(ccl, padded, w)
+        h = padded.shape[0]
+        d = torch.from_numpy(padded).cuda()
+        out = ccl.Analysis(w, h, ccl.node_capacity(w, h), True, "cuda")
+        for call in range(2):
+            out.fg.fill_(-7)
+            out.bg.fill_(-7)
+            ccl.analyze_static(d, w, out)
+            torch.cuda.synchronize()
+            n = out.n
+            assert out.status() == 0, call
+            assert torch.equal(out.counts[:3].cpu(), ref[4]), call
+            assert torch.equal(out.fg.cpu(), ref[0]), call
+            assert torch.equal(out.bg.cpu(), ref[1]), call
+            assert torch.equal(out.parent[:n].cpu(), ref[2]), call
+            assert torch.equal(out.features[:, :n].cpu(), ref[3]), call
+
+
+def test_static_refuses_oversized_images(ccl):
+    lib = ccl._lib
+    w, h = 2048, 1024   # 2 Mpx > the 1 Mpx limit
+    buf = torch.zeros((h, w), dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(4, dtype=torch.int32, device="cuda")
+    par = torch.zeros(16, dtype=torch.int32, device="cuda")
+    feat = torch.zeros((7, 16), dtype=torch.int64, device="cuda")
+    st = lib.ccl_analyze_static(ctypes.c_void_p(buf.data_ptr()), w, h, w, None, None,
+                                ctypes.c_void_p(par.data_ptr()), ctypes.c_void_p(feat.data_ptr()), 16,
+                                ctypes.c_void_p(counts.data_ptr()), None)
+    assert st == ccl.ERR_CAPACITY
+    st = lib.ccl_analyze_static(ctypes.c_void_p(buf.data_ptr()), 5000, 10, 5008, None, None,
+                                ctypes.c_void_p(par.data_ptr()), ctypes.c_void_p(feat.data_ptr()), 16,
+                                ctypes.c_void_p(counts.data_ptr()), None)
+    assert st == ccl.ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert int(counts.abs().sum()) == 0   # nothing was enqueued
