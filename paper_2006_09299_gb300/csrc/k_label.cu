@@ -53,6 +53,13 @@ __global__ void k_prologue(Batch B) {
     B.s.node_fg[d.node0] = 0;
 }
 
+// Valid-pixel mask of word l of a tile row tw pixels wide (0 outside).
+__device__ __forceinline__ uint32_t valid_mask(int tw, int l) {
+    if (l < 0 || l >= WPR) return 0u;
+    const int n = min(max(tw - 32 * l, 0), 32);
+    return n >= 32 ? FULL : ((1u << n) - 1u);
+}
+
 // Run start (tile-local column) of the run holding column x of row r.
 __device__ __forceinline__ int run_start_col(const uint32_t (*sE)[WPR], const uint16_t (*sRS)[WPR],
                                              int r, int x) {
@@ -61,9 +68,10 @@ __device__ __forceinline__ int run_start_col(const uint32_t (*sE)[WPR], const ui
     return m ? (l << 5) + 31 - __clz(m) : (int)sRS[r][l];
 }
 
-// Union every run of row r with the runs of row r - 1 it touches, lane =
-// 32-pixel word. Masks mark, once per pair of touching runs, the column
-// where the pair is tested:
+// Union every run of row r with the runs of row r - 1 it touches, for the
+// contacts whose column lies in word l (32 pixels) and in bits [lo, hi) of
+// that word. Masks mark, once per pair of touching runs, the column where
+// the pair is tested:
 //   va / vb  vertical overlaps of the 8- / 4-adjacent colour, at the first
 //            column of the overlap (where one of the two runs starts);
 //   d1 / d2  diagonal-only contacts of the 8-adjacent colour, up-right and
@@ -72,17 +80,18 @@ __device__ __forceinline__ int run_start_col(const uint32_t (*sE)[WPR], const ui
 template <int CONN>
 __device__ __forceinline__ void unify_rows(uint32_t *par, const uint32_t (*sC)[WPR],
                                            const uint32_t (*sE)[WPR], const uint16_t (*sRS)[WPR], int r,
-                                           int lane, uint32_t vm, bool *ok) {
-    const uint32_t cc = sC[r][lane], cu = sC[r - 1][lane];
-    const uint32_t ec = sE[r][lane], eu = sE[r - 1][lane];
+                                           int l, int tw, uint32_t range, bool *ok) {
+    const uint32_t vm = valid_mask(tw, l), vml = valid_mask(tw, l - 1), vmr = valid_mask(tw, l + 1);
+    const uint32_t cc = sC[r][l], cu = sC[r - 1][l];
+    const uint32_t ec = sE[r][l], eu = sE[r - 1][l];
+    const uint32_t ccl = l ? sC[r][l - 1] : 0u, cul = l ? sC[r - 1][l - 1] : 0u;
+    const uint32_t ccr = l < WPR - 1 ? sC[r][l + 1] : 0u, cur = l < WPR - 1 ? sC[r - 1][l + 1] : 0u;
     const uint32_t ac = CONN ? (~cc & vm) : cc;   // the 8-adjacent colour
     const uint32_t au = CONN ? (~cu & vm) : cu;
     const uint32_t bc = CONN ? cc : (~cc & vm);   // the 4-adjacent colour
     const uint32_t bu = CONN ? cu : (~cu & vm);
-    uint32_t acl = __shfl_up_sync(FULL, ac, 1), acr = __shfl_down_sync(FULL, ac, 1);
-    uint32_t aul = __shfl_up_sync(FULL, au, 1), aur = __shfl_down_sync(FULL, au, 1);
-    if (lane == 0) acl = aul = 0;
-    if (lane == 31) acr = aur = 0;
+    const uint32_t acl = l ? (CONN ? (~ccl & vml) : ccl) : 0u, aul = l ? (CONN ? (~cul & vml) : cul) : 0u;
+    const uint32_t acr = CONN ? (~ccr & vmr) : ccr, aur = CONN ? (~cur & vmr) : cur;
     const uint32_t ac_prev = (ac << 1) | (acl >> 31);   // bit x: pixel x-1
     const uint32_t ac_next = (ac >> 1) | (acr << 31);   // bit x: pixel x+1
     const uint32_t au_prev = (au << 1) | (aul >> 31);
@@ -92,17 +101,17 @@ __device__ __forceinline__ void unify_rows(uint32_t *par, const uint32_t (*sC)[W
     const uint32_t d1 = ac & ~au & au_next & ~ac_next;   // (r,x)-(r-1,x+1)
     const uint32_t d2 = ac & ~au & au_prev & ~ac_prev;   // (r,x)-(r-1,x-1)
     // (a pixel can have both diagonal contacts: d2 gets its own pass)
-    uint32_t m = va | vb | d1;
+    uint32_t m = (va | vb | d1) & range;
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        const int x = 32 * lane + b;
+        const int x = 32 * l + b;
         const int xu = ((d1 >> b) & 1u) ? x + 1 : x;
         local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, xu), ok);
     }
-    m = d2;
+    m = d2 & range;
     while (m) {
-        const int x = 32 * lane + __ffs(m) - 1;
+        const int x = 32 * l + __ffs(m) - 1;
         m &= m - 1;
         local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, x - 1), ok);
     }
@@ -196,18 +205,24 @@ __global__ void __launch_bounds__(LABEL_THREADS, 1) k_label(Batch B) {
         // Warp w first unifies its own row pair (2w, 2w + 1) and points row
         // 2w + 1 at the new roots, like one step of the paper's row-by-row
         // scan. Then blocks of 4, 8, 16 and 32 rows are joined across their
-        // middle row, one boundary per warp and one level at a time, so that
-        // every tree stays a few links deep.
+        // middle row, one level at a time so that every tree stays a few
+        // links deep; each level's contacts are spread over all threads
+        // (a word's 32 columns split into 2, 4, 8 or 16 slices).
         if (2 * warp + 1 < th) {
-            unify_rows<CONN>(par, sC, sE, sRS, 2 * warp + 1, lane, vm, &ok);
+            unify_rows<CONN>(par, sC, sE, sRS, 2 * warp + 1, lane, tw, FULL, &ok);
             __syncwarp();
             compress_row(par, sE, 2 * warp + 1, lane, &ok);
         }
 #pragma unroll 1
         for (int bs = 4; bs <= TH; bs *= 2) {
             __syncthreads();
-            const int r = bs * warp + bs / 2;
-            if (warp < TH / bs && r < th) unify_rows<CONN>(par, sC, sE, sRS, r, lane, vm, &ok);
+            const int parts = LABEL_THREADS / ((TH / bs) * WPR);   // slices per word
+            const int t = threadIdx.x;
+            const int j = t / (WPR * parts), l = (t / parts) % WPR, q = t % parts;
+            const int r = bs * j + bs / 2;
+            const int span = 32 / parts;
+            const uint32_t range = (span == 32 ? FULL : (((1u << span) - 1u) << (q * span)));
+            if (r < th && 32 * l < tw) unify_rows<CONN>(par, sC, sE, sRS, r, l, tw, range, &ok);
         }
         __syncthreads();
 
