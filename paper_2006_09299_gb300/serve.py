@@ -1,0 +1,335 @@
+"""Continuous-batching serving loop for connected component analysis.
+
+Frames (uint8 host arrays of mixed sizes) arrive one by one. The server
+  - admits a waiting frame when a resident slot of its size class is free,
+    or when the device-memory budget allows a new one (label images, tree,
+    features and the image buffer stay resident per slot and are reused);
+  - every tick launches the admitted frames as ONE batched analysis
+    (ccl_analyze_batched + ccl_fill_holes_batched) on the next free CUDA
+    stream; each stream has its own batched context, so a new tick runs on
+    the device while earlier ticks are still in flight;
+  - completes a request when its batch's CUDA event has fired: its results
+    are the slot's device tensors, and latency = completion - arrival.
+
+The scheduling logic (admission, batching, stream rotation, completion) is
+plain Python over a backend object; GpuBackend drives the CUDA library, and
+tests substitute a fake backend to check the host logic without a GPU.
+"""
+import collections
+import math
+import threading
+import time
+
+import numpy as np
+
+
+class Request:
+    __slots__ = ("rid", "frame", "t_arrive", "t_admit", "t_launch", "t_done", "slot", "done", "cancelled",
+                 "result", "status")
+
+    def __init__(self, rid, frame, t_arrive):
+        self.rid = rid
+        self.frame = frame
+        self.t_arrive = t_arrive
+        self.t_admit = self.t_launch = self.t_done = None
+        self.slot = None
+        self.done = threading.Event()
+        self.cancelled = False
+        self.result = None
+        self.status = None
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.t_arrive
+
+
+class Slot:
+    """Resident buffers for one frame of a size class (allocated by the backend)."""
+
+    def __init__(self, key, nbytes, handle):
+        self.key = key
+        self.nbytes = nbytes
+        self.handle = handle
+
+
+class Server:
+    def __init__(self, backend, memory_budget, max_batch=16, n_streams=2, fill_threshold=64):
+        self.backend = backend
+        self.budget = int(memory_budget)
+        self.max_batch = int(max_batch)
+        self.n_streams = int(n_streams)
+        self.fill_threshold = fill_threshold
+        self.used = 0
+        self.free_slots = collections.defaultdict(list)   # size key -> [Slot]
+        self.waiting = collections.deque()
+        self.admitted = collections.deque()
+        self.inflight = []                                 # (stream, handle, [Request])
+        self.stream_busy = [False] * self.n_streams
+        self.next_stream = 0
+        self.completed = []
+        self.lock = threading.Lock()
+        self.wake = threading.Event()
+        self._stop = False
+        self._thread = None
+        self._rid = 0
+        self.ticks = 0
+
+    # ------------------------------------------------------------ clients
+    def submit(self, frame, t_arrive=None):
+        with self.lock:
+            r = Request(self._rid, frame, time.perf_counter() if t_arrive is None else t_arrive)
+            self._rid += 1
+            self.waiting.append(r)
+        self.wake.set()
+        return r
+
+    def cancel(self, req):
+        """Cancel a request that has not been launched yet."""
+        with self.lock:
+            if req.t_launch is None and not req.done.is_set():
+                req.cancelled = True
+                try:
+                    self.waiting.remove(req)
+                except ValueError:
+                    try:
+                        self.admitted.remove(req)
+                    except ValueError:
+                        pass
+                    self._release(req)
+                req.done.set()
+                return True
+        return False
+
+    # ---------------------------------------------------------- scheduling
+    def _release(self, req):
+        if req.slot is not None:
+            self.free_slots[req.slot.key].append(req.slot)
+            req.slot = None
+
+    def _admit(self):
+        while self.waiting:
+            r = self.waiting[0]
+            key = self.backend.size_key(r.frame)
+            if self.free_slots[key]:
+                r.slot = self.free_slots[key].pop()
+            else:
+                need = self.backend.slot_bytes(key)
+                if self.used + need > self.budget:
+                    if self._evict_for(need):
+                        continue
+                    break            # wait for memory: frames are admitted in arrival order
+                r.slot = self.backend.alloc_slot(key)
+                self.used += r.slot.nbytes
+            r.t_admit = time.perf_counter()
+            self.waiting.popleft()
+            self.admitted.append(r)
+
+    def _evict_for(self, need):
+        """Free idle slots of other size classes until `need` bytes fit."""
+        freed = False
+        for key in list(self.free_slots):
+            while self.free_slots[key] and self.used + need > self.budget:
+                s = self.free_slots[key].pop()
+                self.backend.free_slot(s)
+                self.used -= s.nbytes
+                freed = True
+        return freed and self.used + need <= self.budget
+
+    def _launch(self):
+        while self.admitted:
+            k = None
+            for j in range(self.n_streams):
+                c = (self.next_stream + j) % self.n_streams
+                if not self.stream_busy[c]:
+                    k = c
+                    break
+            if k is None:
+                return
+            batch = []
+            while self.admitted and len(batch) < self.max_batch:
+                batch.append(self.admitted.popleft())
+            now = time.perf_counter()
+            for r in batch:
+                r.t_launch = now
+            handle = self.backend.launch(k, batch, self.fill_threshold)
+            self.stream_busy[k] = True
+            self.inflight.append((k, handle, batch))
+            self.next_stream = (k + 1) % self.n_streams
+            self.ticks += 1
+
+    def _complete(self):
+        still = []
+        for k, handle, batch in self.inflight:
+            if self.backend.done(handle):
+                now = time.perf_counter()
+                results = self.backend.results(handle, batch)
+                for r, res in zip(batch, results):
+                    r.result, r.status = res
+                    r.t_done = now
+                    self.completed.append(r)
+                    r.done.set()
+                self.stream_busy[k] = False
+                self.backend.retire(handle)
+            else:
+                still.append((k, handle, batch))
+        self.inflight = still
+
+    def release(self, req):
+        """Give a finished request's slot back (its result tensors are reused)."""
+        with self.lock:
+            self._release(req)
+        self.wake.set()
+
+    def step(self):
+        """One scheduler pass: completions, admission, launches."""
+        with self.lock:
+            self._complete()
+            self._admit()
+            self._launch()
+            return bool(self.waiting or self.admitted or self.inflight)
+
+    # --------------------------------------------------------------- loop
+    def start(self, poll_s=20e-6, switch_interval=2e-4):
+        # the scheduler shares the interpreter with the clients: a short GIL
+        # switch interval keeps its reaction time well under a millisecond
+        import sys
+        self._old_switch = sys.getswitchinterval()
+        sys.setswitchinterval(switch_interval)
+
+        def loop():
+            while not self._stop:
+                busy = self.step()
+                if not busy:
+                    self.wake.wait(0.002)
+                    self.wake.clear()
+                else:
+                    time.sleep(poll_s)
+        self._thread = threading.Thread(target=loop, daemon=True)
+        self._thread.start()
+
+    def stop(self):
+        self._stop = True
+        self.wake.set()
+        if self._thread is not None:
+            self._thread.join()
+            import sys
+            sys.setswitchinterval(self._old_switch)
+
+    def queue_depth(self):
+        with self.lock:
+            return len(self.waiting) + len(self.admitted)
+
+
+# ----------------------------------------------------------------- backend
+
+
+class GpuBackend:
+    """Runs batches through the CUDA library on n_streams streams."""
+
+    def __init__(self, n_streams=2, max_batch=16, max_side=3840, max_frame_px=3840 * 2160, device=0,
+                 capacity_fraction=16):
+        import torch
+        from . import ccl
+        self.torch = torch
+        self.ccl = ccl
+        self.dev = torch.device("cuda", device)
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(n_streams)]
+        # batch compositions vary from tick to tick: plain launches, no graph cache
+        self.ctxs = [ccl.BatchContext(max_batch, max_batch * max_frame_px, max_side, graph_cache=False)
+                     for _ in range(n_streams)]
+        self.capacity_fraction = capacity_fraction
+
+    @staticmethod
+    def size_key(frame):
+        return frame.shape
+
+    def _cap(self, key):
+        h, w = key
+        return min(self.ccl.node_capacity(w, h), max(4096, (w * h) // self.capacity_fraction))
+
+    def slot_bytes(self, key):
+        h, w = key
+        pitch = -(-w // 16) * 16
+        cap = self._cap(key)
+        return h * pitch + 8 * h * w + cap * (4 + 56 + 4 + 56 + 4) + 16
+
+    def alloc_slot(self, key):
+        torch = self.torch
+        h, w = key
+        pitch = -(-w // 16) * 16
+        img = torch.empty((h, pitch), dtype=torch.uint8, device=self.dev)
+        out = self.ccl.Analysis(w, h, self._cap(key), True, self.dev).alloc_fill()
+        host = torch.empty((h, pitch), dtype=torch.uint8).pin_memory()
+        return Slot(key, self.slot_bytes(key), (img, out, host, w))
+
+    def free_slot(self, slot):
+        slot.handle = None
+
+    def launch(self, k, batch, fill_threshold):
+        torch = self.torch
+        st = self.streams[k]
+        with torch.cuda.stream(st):
+            imgs, outs = [], []
+            for r in batch:
+                img, out, host, w = r.slot.handle
+                host[:, :w].copy_(torch.from_numpy(r.frame))
+                img.copy_(host, non_blocking=True)
+                imgs.append((img, w))
+                outs.append(out)
+            self.ctxs[k].analyze(imgs, outs=outs, stream=st)
+            self.ctxs[k].fill_holes(fill_threshold, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return ev
+
+    def done(self, handle):
+        return handle.query()
+
+    def results(self, handle, batch):
+        return [(r.slot.handle[1], None) for r in batch]
+
+    def retire(self, handle):
+        pass
+
+
+# ----------------------------------------------------------------- driver
+
+
+def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True):
+    """Submit frames (cycled) with Poisson arrivals at rate_hz for duration_s;
+    wait for the admitted work to finish. Returns the completed requests and
+    the queue depth seen at the end of the arrival window."""
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    t_next = t0
+    reqs = []
+    i = 0
+    while True:
+        t_next += rng.exponential(1.0 / rate_hz)
+        if t_next - t0 > duration_s:
+            break
+        wait = t_next - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)          # releases the interpreter to the scheduler
+        reqs.append(server.submit(frames[i % len(frames)], t_arrive=t_next))
+        i += 1
+        # hand back the slots of finished requests (their results were consumed)
+        if release:
+            for r in reqs[max(0, len(reqs) - 64):]:
+                if r.done.is_set() and r.slot is not None:
+                    server.release(r)
+    depth_end = server.queue_depth()
+    for r in reqs:
+        r.done.wait(30.0)
+        if release and r.slot is not None:
+            server.release(r)
+    return reqs, depth_end
+
+
+def latency_stats(reqs):
+    lat = sorted(r.latency for r in reqs if r.latency is not None)
+    if not lat:
+        return {"p50_ms": None, "p99_ms": None, "n": 0}
+    def q(p):
+        return lat[min(len(lat) - 1, int(math.ceil(p * len(lat))) - 1)] * 1e3
+    return {"p50_ms": round(q(0.50), 3), "p99_ms": round(q(0.99), 3), "n": len(lat)}

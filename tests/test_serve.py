@@ -1,0 +1,161 @@
+"""Serving loop: host logic with a fake backend (CPU), and results alone vs
+in a mix on the GPU."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2006_09299_gb300 import inputs
+from paper_2006_09299_gb300.serve import Server, Slot, latency_stats, poisson_run
+
+
+class FakeBackend:
+    """Completes each batch `delay` seconds after launch; records launches."""
+
+    def __init__(self, delay=0.002, nbytes=100):
+        self.delay = delay
+        self.nbytes = nbytes
+        self.launches = []
+        self.alloc = 0
+        self.freed = 0
+
+    def size_key(self, frame):
+        return frame.shape
+
+    def slot_bytes(self, key):
+        return self.nbytes * key[0] * key[1]
+
+    def alloc_slot(self, key):
+        self.alloc += 1
+        return Slot(key, self.slot_bytes(key), object())
+
+    def free_slot(self, slot):
+        self.freed += 1
+
+    def launch(self, k, batch, T):
+        self.launches.append((k, [r.rid for r in batch]))
+        return time.perf_counter() + self.delay
+
+    def done(self, handle):
+        return time.perf_counter() >= handle
+
+    def results(self, handle, batch):
+        return [("res%d" % r.rid, 0) for r in batch]
+
+    def retire(self, handle):
+        pass
+
+
+def drain(s, limit=5.0):
+    t = time.perf_counter()
+    while s.step() and time.perf_counter() - t < limit:
+        time.sleep(0.0005)
+
+
+def test_batches_respect_max_batch_and_streams():
+    be = FakeBackend(delay=0.01)
+    s = Server(be, memory_budget=10**9, max_batch=4, n_streams=2)
+    reqs = [s.submit(np.zeros((2, 3), np.uint8)) for _ in range(10)]
+    s.step()
+    # two streams busy, 4 + 4 launched, 2 still admitted
+    assert [len(b) for _, b in be.launches] == [4, 4]
+    assert {k for k, _ in be.launches} == {0, 1}
+    drain(s)
+    assert all(r.done.is_set() and r.result == "res%d" % r.rid for r in reqs)
+    assert sorted(rid for _, b in be.launches for rid in b) == list(range(10))
+
+
+def test_continuous_batching_admits_while_in_flight():
+    be = FakeBackend(delay=0.02)
+    s = Server(be, memory_budget=10**9, max_batch=8, n_streams=2)
+    a = [s.submit(np.zeros((4, 4), np.uint8)) for _ in range(3)]
+    s.step()
+    b = [s.submit(np.zeros((4, 4), np.uint8)) for _ in range(3)]
+    s.step()   # second stream takes the new arrivals while the first batch runs
+    assert len(be.launches) == 2 and be.launches[1][1] == [r.rid for r in b]
+    drain(s)
+    assert all(r.done.is_set() for r in a + b)
+    assert max(r.t_launch for r in b) < min(r.t_done for r in a)   # overlapped
+
+
+def test_memory_budget_admission_and_slot_reuse():
+    be = FakeBackend(delay=0.001, nbytes=1)
+    s = Server(be, memory_budget=2 * 100, max_batch=8, n_streams=1)   # room for two 10x10 slots
+    reqs = [s.submit(np.zeros((10, 10), np.uint8)) for _ in range(6)]
+    s.step()
+    assert len(s.admitted) + sum(len(b) for _, _, b in s.inflight) == 2
+    assert s.used <= s.budget
+    for _ in range(200):
+        s.step()
+        for r in reqs:
+            if r.done.is_set() and r.slot is not None:
+                s.release(r)
+        if all(r.done.is_set() for r in reqs):
+            break
+        time.sleep(0.001)
+    assert all(r.done.is_set() for r in reqs)
+    assert be.alloc == 2          # slots reused, never more than the budget allows
+    # a larger size class evicts idle slots to fit
+    big = s.submit(np.zeros((14, 14), np.uint8))
+    drain(s)
+    assert big.done.is_set() and be.freed >= 1 and s.used <= s.budget
+
+
+def test_cancel_before_launch():
+    be = FakeBackend(delay=0.05)
+    s = Server(be, memory_budget=10**9, max_batch=1, n_streams=1)
+    r1 = s.submit(np.zeros((2, 2), np.uint8))
+    s.step()
+    r2 = s.submit(np.zeros((2, 2), np.uint8))
+    assert s.cancel(r2) and r2.cancelled and r2.done.is_set()
+    assert not s.cancel(r1)       # already launched
+    drain(s)
+    assert [rid for _, b in be.launches for rid in b] == [r1.rid]
+
+
+def test_poisson_driver_and_latency_stats():
+    be = FakeBackend(delay=0.001)
+    s = Server(be, memory_budget=10**9, max_batch=8, n_streams=2)
+    s.start()
+    try:
+        reqs, depth = poisson_run(s, [np.zeros((3, 3), np.uint8)], rate_hz=2000, duration_s=0.2)
+    finally:
+        s.stop()
+    st = latency_stats(reqs)
+    assert st["n"] == len(reqs) > 100
+    assert 0 < st["p50_ms"] <= st["p99_ms"]
+
+
+@pytest.mark.gpu
+def test_results_alone_and_in_the_mix_are_identical():
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2006_09299_gb300 import ccl
+    from paper_2006_09299_gb300.serve import GpuBackend
+
+    frames = inputs.frame_stream(seed=5, n=12)
+    be = GpuBackend(n_streams=2, max_batch=4)
+    s = Server(be, memory_budget=8 << 30, max_batch=4, n_streams=2)
+    s.start()
+    try:
+        reqs = [s.submit(f) for f in frames]
+        for r in reqs:
+            assert r.done.wait(60)
+    finally:
+        s.stop()
+    torch.cuda.synchronize()
+    for f, r in zip(frames, reqs):
+        h, w = f.shape
+        pitch = -(-w // 16) * 16
+        ctx = ccl.Context(w, h, pitch)
+        alone = ctx.analyze(torch.from_numpy(inputs.pitched(f, pitch, 0)).cuda())
+        n, _, _, st = ctx.get_counts()
+        mix = r.result
+        assert st == 0 and mix.status() == 0
+        assert mix.n == n
+        assert torch.equal(mix.fg, alone.fg) and torch.equal(mix.bg, alone.bg)
+        assert torch.equal(mix.parent[:n], alone.parent[:n])
+        assert torch.equal(mix.features[:, :n], alone.features[:, :n])
+        ctx.close()
