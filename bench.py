@@ -200,6 +200,8 @@ def run_ours(args, rank, world, local_rank):
         ctx.analyze(d_imgs, outs=outs)
         ctx.fill_holes(FILL_T)
 
+    tuning = pick_tile_rows(args, ctx, step, shapes)
+
     def barrier():
         if world > 1:
             torch.distributed.barrier()
@@ -268,7 +270,8 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded generators shaped like the paper's workloads)",
-        "config": dict(workload_desc(args.workload, imgs), parallelism="replicas" if world > 1 else "single"),
+        "config": dict(workload_desc(args.workload, imgs), parallelism="replicas" if world > 1 else "single",
+                       tile=tuning),
         "roofline": roofline,
         "path_roofline": {"bytes_per_pixel": PATH_BYTES_PER_PX, "achieved": round(path_gbs, 1), "peak": peak,
                           "unit": "GB/s", "frac": round(path_gbs / peak, 4)},
@@ -279,6 +282,19 @@ def run_ours(args, rank, world, local_rank):
     }
     res.update(extra)
     return res
+
+
+def pick_tile_rows(args, ctx, step, shapes):
+    """Tile height: fixed by --tile-rows, or chosen by the autotuner (a fresh
+    timing of this step under each height, CUDA events)."""
+    from paper_2006_09299_gb300 import autotune
+    if args.tile_rows != "auto":
+        ctx.set_tile_rows(int(args.tile_rows))
+        return {"rows": int(args.tile_rows), "cols": 1024, "chosen_by": "flag"}
+    path = os.path.join(tempfile.mkdtemp(), "tune.json")
+    rows, times = autotune.tune(ctx, step, autotune.size_class(shapes), cache_path=path, reps=3, warmup=2)
+    return {"rows": rows, "cols": 1024, "chosen_by": "autotuner",
+            "ms_per_step": {str(k): round(v, 4) for k, v in times.items()}}
 
 
 def run_e2e(args, ctx, imgs, outs, dev, stream, px):
@@ -341,6 +357,10 @@ def batched_vs_plain(ccl, dev, stream, reps=5):
     bctx = ccl.BatchContext(len(imgs), px, 2048)
     outs = bctx.new_outputs(shapes, labels=True, fill=False, device=dev)
     pctx = ccl.BatchContext(1, 2048 * 2048, 2048, graph_cache=False)
+    from paper_2006_09299_gb300 import autotune
+    rows, times = autotune.tune(bctx, lambda: bctx.analyze(d_imgs, outs=outs), autotune.size_class(shapes),
+                                cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=3, warmup=2)
+    pctx.set_tile_rows(rows)
 
     def batched():
         bctx.analyze(d_imgs, outs=outs)
@@ -367,7 +387,8 @@ def batched_vs_plain(ccl, dev, stream, reps=5):
     return {"workload": "uneven256 (256 images, %.1f Mpx)" % (px / 1e6),
             "batched_ms": round(res["batched"], 3), "plain_ms": round(res["plain"], 3),
             "batched_gpx_s": round(px / res["batched"] / 1e6, 2), "plain_gpx_s": round(px / res["plain"] / 1e6, 2),
-            "ratio": round(res["plain"] / res["batched"], 2)}
+            "ratio": round(res["plain"] / res["batched"], 2),
+            "tile_rows": rows, "tuning_ms": {str(k): round(v, 4) for k, v in times.items()}}
 
 
 # ------------------------------------------------------------ reference arm
@@ -493,6 +514,7 @@ def main():
     ap.add_argument("--subset", type=int, default=0, help="use only the first k images of the workload")
     ap.add_argument("--tight", action="store_true", help="node arrays sized w*h/4 instead of the bound")
     ap.add_argument("--pick", default="", help="comma-separated image indices of the workload to use")
+    ap.add_argument("--tile-rows", default="auto", choices=["auto", "16", "32"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()

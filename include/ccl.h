@@ -182,6 +182,11 @@ ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, i
 /* Hole filling for every image of the last batch that has fill buffers. */
 ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stream_t stream);
 
+/* Tile height for later analyses of this context: 32 rows (default) or 16
+ * rows of 1024 columns. Results are identical; the speed differs with the
+ * image (ccl.autotune picks one per size class by timing both). */
+ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows);
+
 /* Enable (1) or disable (0) the CUDA-graph cache of ccl_analyze_batched and
  * ccl_analyze. */
 ccl_status ccl_set_graph_cache(ccl_ctx *ctx, int32_t enable);

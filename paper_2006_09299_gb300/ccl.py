@@ -48,6 +48,7 @@ SIGNATURES = {
     "ccl_analyze_batched": (ctypes.c_int, [_p, ctypes.POINTER(ImageDesc), _i32, _p]),
     "ccl_fill_holes_batched": (ctypes.c_int, [_p, _i64, _p]),
     "ccl_set_graph_cache": (ctypes.c_int, [_p, _i32]),
+    "ccl_set_tile_rows": (ctypes.c_int, [_p, _i32]),
     "ccl_enable_phase_timing": (ctypes.c_int, [_p, _i32]),
     "ccl_read_phase_timing": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "ccl_get_launch_count": (ctypes.c_int, [_p, ctypes.POINTER(_i64)]),
@@ -112,6 +113,10 @@ class _Instrumented:
 
     def set_graph_cache(self, enable):
         _check(_lib.ccl_set_graph_cache(self._h, 1 if enable else 0), "ccl_set_graph_cache")
+
+    def set_tile_rows(self, rows):
+        _check(_lib.ccl_set_tile_rows(self._h, int(rows)), "ccl_set_tile_rows")
+        self.tile_rows = int(rows)
 
 
 class Analysis:

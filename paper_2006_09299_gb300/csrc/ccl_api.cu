@@ -40,6 +40,7 @@ struct Limits {
 
 struct Plan {
     std::vector<ImgDesc> d;
+    int32_t th = TH_MAX;
     Limits need;
     int32_t n_tiles = 0;
     int64_t n_segs = 0, n_h = 0, n_v = 0, n_p = 0;
@@ -78,6 +79,7 @@ struct ccl_ctx {
     bool batched = false;
     int32_t w = 0, h = 0, pitch = 0;    // fixed shape of a single-image context
     int32_t conn = 0;
+    int32_t th = TH_MAX;                // tile height (16 or 32)
     Limits cap;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -112,12 +114,13 @@ static Limits limits_of_bounds(int64_t images, int64_t pixels, int64_t max_side)
     Limits L;
     L.images = images;
     L.pixels = pixels;
-    // tiles of one image <= (h/TH + 1)(w/TW + 1) <= wh/(TH TW) + h/TH + w/TW + 1
-    L.tiles = pixels / (TH * TW) + images * (max_side / TH + max_side / TW + 1);
+    // tiles of one image <= (h/TH + 1)(w/TW + 1) <= wh/(TH TW) + h/TH + w/TW + 1,
+    // sized for the smaller tile height so that both can run
+    L.tiles = pixels / (TH_MIN * TW) + images * (max_side / TH_MIN + max_side / TW + 1);
     // tile rows (segments) = h * ceil(w/TW) <= wh/TW + h
     L.segs = pixels / TW + images * max_side;
     // edge cells = 2 w TY + 2 h TX <= 2wh/TH + 2w + 2wh/TW + 2h
-    L.edges = 2 * pixels / TH + 2 * pixels / TW + images * 4 * max_side;
+    L.edges = 2 * pixels / TH_MIN + 2 * pixels / TW + images * 4 * max_side;
     L.ncap = (3 * pixels) / 4 + images * (max_side / 2 + 3);
     return L;
 }
@@ -184,8 +187,9 @@ static ccl_status check_image(const ccl_image_desc &x) {
     return CCL_OK;
 }
 
-static ccl_status build_plan(const ccl_image_desc *in, int n, Plan *P) {
+static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, Plan *P) {
     P->d.assign(n, ImgDesc{});
+    P->th = th;
     int64_t tiles = 0, segs = 0, px = 0, edges = 0, ncap = 0, hi = 0, vi = 0, pi = 0;
     bool any_labels = false;
     for (int i = 0; i < n; ++i) {
@@ -207,7 +211,7 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, Plan *P) {
         d.h = x.h;
         d.pitch = x.pitch;
         d.TX = (x.w + TW - 1) / TW;
-        d.TY = (x.h + TH - 1) / TH;
+        d.TY = (x.h + th - 1) / th;
         d.tile0 = (int32_t)tiles;
         d.seg0 = segs;
         d.px0 = px;
@@ -248,6 +252,7 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, Plan *P) {
 static Batch make_batch(const ccl_ctx *c, const Plan &P) {
     Batch B;
     B.desc = c->d_desc;
+    B.th = P.th;
     B.n_img = (int32_t)P.d.size();
     B.n_tiles = P.n_tiles;
     B.n_segs = P.n_segs;
@@ -294,6 +299,7 @@ static const cudaEvent_t *timing_slot(ccl_ctx *c, int kind) {
 static Shape shape_of(const ccl_ctx *c, const Plan &P) {
     Shape s;
     s.v.push_back(c->conn);
+    s.v.push_back(P.th);
     for (const ImgDesc &d : P.d) {
         s.v.push_back(d.w);
         s.v.push_back(d.h);
@@ -376,7 +382,9 @@ ccl_status ccl_create(ccl_ctx **out, int32_t w, int32_t h, int32_t pitch) {
     c->w = w;
     c->h = h;
     c->pitch = pitch;
-    const int64_t TX = (w + TW - 1) / TW, TY = (h + TH - 1) / TH;
+    // sized for the smaller tile height (more tiles and edge cells) so that
+    // both tile heights can run
+    const int64_t TX = (w + TW - 1) / TW, TY = (h + TH_MIN - 1) / TH_MIN;
     Limits L;
     L.images = 1;
     L.tiles = TX * TY;
@@ -414,7 +422,7 @@ ccl_status ccl_analyze(ccl_ctx *ctx, const uint8_t *d_img, int32_t *d_fg_labels,
     x.counts = d_counts;
     x.capacity = formula_capacity(ctx->w, ctx->h);
     Plan P;
-    ccl_status st = build_plan(&x, 1, &P);
+    ccl_status st = build_plan(&x, 1, ctx->th, &P);
     if (st != CCL_OK) return st;
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
@@ -477,7 +485,7 @@ ccl_status ccl_create_batched(ccl_ctx **out, int32_t max_images, int64_t max_tot
 ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, int32_t n, ccl_stream_t stream) {
     if (!ctx || !ctx->batched || !host_descs || n <= 0) return CCL_ERR_ARG;
     Plan P;
-    ccl_status st = build_plan(host_descs, n, &P);
+    ccl_status st = build_plan(host_descs, n, ctx->th, &P);
     if (st != CCL_OK) return st;
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
@@ -486,6 +494,12 @@ ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stre
     if (!ctx || !ctx->batched) return CCL_ERR_ARG;
     if (!ctx->have_last) return CCL_ERR_STATE;
     return fill_last(ctx, area_threshold, (cudaStream_t)stream);
+}
+
+ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows) {
+    if (!ctx || (rows != 16 && rows != 32)) return CCL_ERR_ARG;
+    ctx->th = rows;
+    return CCL_OK;
 }
 
 ccl_status ccl_set_graph_cache(ccl_ctx *ctx, int32_t enable) {

@@ -24,13 +24,11 @@ namespace ccl {
 
 constexpr int TW = 1024;               // tile width in pixels (32 words)
 constexpr int WPR = TW / 32;           // 32-bit words per tile row = lanes
-constexpr int TH = 32;                 // tile height in rows
-constexpr int TILE_PX = TH * TW;       // 32768: local pixel index fits 15 bits
+constexpr int TH_MAX = 32;             // tile height in rows: 32 (default) or 16,
+constexpr int TH_MIN = 16;             // chosen per context (ccl_set_tile_rows)
+constexpr int TILE_PX = TH_MAX * TW;   // 32768: local pixel index fits 15 bits
 constexpr int NTHREADS = 256;          // threads of the write / resolve / canon kernels
-constexpr int LABEL_THREADS = 512;     // threads of the labelling kernel: two rows per warp
-constexpr int LABEL_WARPS = LABEL_THREADS / 32;
 constexpr int NWARPS = NTHREADS / 32;
-constexpr int MAXR = 4096;             // local roots with on-chip feature records
 constexpr int SCAN_B = 256;            // segments per block of the node scan
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -91,6 +89,7 @@ struct Scratch {
 
 struct Batch {
     const ImgDesc *desc;
+    int32_t th;                // tile height of this call (16 or 32)
     int32_t n_img;
     int32_t n_tiles;
     int64_t n_segs;
@@ -184,7 +183,7 @@ struct TileGeo {
     int64_t px, b;
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const ImgDesc &d, int lt) {
+__device__ __forceinline__ TileGeo tile_geo(const ImgDesc &d, int lt, int TH) {
     TileGeo g;
     g.ty = lt / d.TX;
     g.tx = lt - g.ty * d.TX;

@@ -99,7 +99,7 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     d.h = h;
     d.pitch = pitch;
     d.TX = (w + TW - 1) / TW;
-    d.TY = (h + TH - 1) / TH;
+    d.TY = (h + TH_MAX - 1) / TH_MAX;
     const int64_t full = ((int64_t)(h + 1) / 2) * ((w + 1) / 2) + ((int64_t)w * h + 1) / 2 + 1;
     d.ncap = capacity < full ? capacity : full;
     d.vec = (w % 4 == 0) && d_fg_labels && ((uintptr_t)d_fg_labels % 16 == 0) && ((uintptr_t)d_bg_labels % 16 == 0);
@@ -140,6 +140,7 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     d.seg0 = d.px0 = d.b0 = d.node0 = 0;
     Batch B;
     B.desc = (const ImgDesc *)(p + desc_off);
+    B.th = TH_MAX;
     B.n_img = 1;
     B.n_tiles = (int32_t)tiles;
     B.n_segs = segs;

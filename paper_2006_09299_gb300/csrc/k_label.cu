@@ -129,11 +129,13 @@ __device__ __forceinline__ void compress_row(uint32_t *par, const uint32_t (*sE)
     }
 }
 
-template <int CONN>
-__global__ void __launch_bounds__(LABEL_THREADS, 1) k_label(Batch B) {
+template <int CONN, int TH>
+__global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
+    constexpr int LABEL_THREADS = TH * 16;   // two rows per warp
+    constexpr int LABEL_WARPS = TH / 2;
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *par = (uint32_t *)smem;                                    // 128 KB
-    uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(smem + TILE_PX * 4);         // colour bits
+    uint32_t *par = (uint32_t *)smem;                                    // 4 B per tile pixel
+    uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(smem + TH * TW * 4);         // colour bits
     uint32_t(*sE)[WPR] = sC + TH;                                        // run starts
     uint32_t(*sR)[WPR] = sE + TH;                                        // local roots
     uint32_t(*sB)[WPR] = sR + TH;                                        // border roots
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(LABEL_THREADS, 1) k_label(Batch B) {
         const int t = sTile;
         if (t >= B.n_tiles) break;
         const ImgDesc &d = B.desc[sImg];
-        const TileGeo g = tile_geo(d, t - d.tile0);
+        const TileGeo g = tile_geo(d, t - d.tile0, TH);
         const int tx = g.tx, y0 = g.y0, x0 = g.x0, th = g.th, tw = g.tw;
         const int64_t rowwords = (int64_t)d.TX * WPR;
         const int64_t plane0 = (d.seg0 + (int64_t)y0 * d.TX + tx) * WPR;  // word (y0, tile col)
@@ -273,8 +275,8 @@ __global__ void __launch_bounds__(LABEL_THREADS, 1) k_label(Batch B) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 int tot;
-                const int ex = warp_excl_sum(sRowTot[k][lane], &tot);
-                sRowTot[k][lane] = ex;
+                const int ex = warp_excl_sum(lane < TH ? sRowTot[k][lane] : 0, &tot);
+                if (lane < TH) sRowTot[k][lane] = ex;
                 if (lane == 0) sTot[k] = tot;
             }
         }
@@ -347,24 +349,35 @@ __global__ void __launch_bounds__(LABEL_THREADS, 1) k_label(Batch B) {
     }
 }
 
-constexpr size_t LABEL_SMEM = TILE_PX * 4 + 4 * TH * WPR * 4 + 4 * TH * WPR * 2;
+template <int TH>
+constexpr size_t label_smem() { return (size_t)TH * TW * 4 + 4 * TH * WPR * 4 + 4 * TH * WPR * 2; }
 
 void launch_prologue(const Batch &B, cudaStream_t st) {
     k_prologue<<<(B.n_img + 127) / 128, 128, 0, st>>>(B);
 }
 
 void launch_label(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    const int grid = min(B.n_tiles, c.sms);
-    if (B.conn == 0)
-        k_label<0><<<grid, LABEL_THREADS, LABEL_SMEM, st>>>(B);
-    else
-        k_label<1><<<grid, LABEL_THREADS, LABEL_SMEM, st>>>(B);
+    if (B.th == 32) {
+        const int grid = min(B.n_tiles, c.sms);
+        if (B.conn == 0)
+            k_label<0, 32><<<grid, 512, label_smem<32>(), st>>>(B);
+        else
+            k_label<1, 32><<<grid, 512, label_smem<32>(), st>>>(B);
+    } else {
+        const int grid = min(B.n_tiles, 2 * c.sms);
+        if (B.conn == 0)
+            k_label<0, 16><<<grid, 256, label_smem<16>(), st>>>(B);
+        else
+            k_label<1, 16><<<grid, 256, label_smem<16>(), st>>>(B);
+    }
 }
 
 cudaError_t configure_label() {
-    cudaError_t e = cudaFuncSetAttribute(k_label<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LABEL_SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_label<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LABEL_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_label<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_label<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_label<0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<16>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_label<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<16>());
+    return e;
 }
 
 }  // namespace ccl

@@ -34,7 +34,7 @@ enum { TOP, BOTTOM, LEFT, RIGHT };
 // Union-find slot of the border root that owns edge cell `pos` (a column for
 // TOP / BOTTOM, a row for LEFT / RIGHT) of tile lt.
 __device__ __forceinline__ uint32_t edge_slot(const Batch &B, const ImgDesc &d, int lt, int side, int pos) {
-    const TileGeo g = tile_geo(d, lt);
+    const TileGeo g = tile_geo(d, lt, B.th);
     const int off = side == TOP ? edge_top(g, pos) : side == BOTTOM ? edge_bottom(g, pos)
                   : side == LEFT ? edge_left(g, pos) : edge_right(g, pos);
     return (uint32_t)(B.n_img + g.b) + B.s.edges[g.b + off];
@@ -62,7 +62,7 @@ __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool 
     const int j = (int)(item - (int64_t)bb * words);
     const int x = 32 * j;
     if (x >= d.w) return;
-    const int yu = (bb + 1) * TH - 1, yd = yu + 1;
+    const int yu = (bb + 1) * B.th - 1, yd = yu + 1;
     const int vcnt = min(d.w - x, 32);
     const uint32_t vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
     const uint32_t cu = plane_word(B, d, yu, j), cd = plane_word(B, d, yd, j);
@@ -113,8 +113,8 @@ __device__ void merge_cols(const Batch &B, const ImgDesc &d, int64_t item, bool 
     const int vb = (int)(item / d.h);          // boundary between tile columns vb and vb+1
     const int y = (int)(item - (int64_t)vb * d.h);
     const int x0 = (vb + 1) * TW;
-    const int ty = y / TH, r = y - ty * TH;
-    const int th = min(TH, d.h - ty * TH);
+    const int ty = y / B.th, r = y - ty * B.th;
+    const int th = min(B.th, d.h - ty * B.th);
     const int ltl = ty * d.TX + vb, ltr = ltl + 1;
     const bool cl = pixel_fg(B, d, y, x0 - 1), cr = pixel_fg(B, d, y, x0);
     if (cl == cr) {
@@ -164,7 +164,7 @@ __device__ void merge_perimeter(const Batch &B, const ImgDesc &d, int img, int64
     const int y = (int)(item - 2 * words - (right ? d.h : 0));
     const int x = right ? d.w - 1 : 0;
     if (pixel_fg(B, d, y, x)) return;
-    const int ty = y / TH, r = y - ty * TH;
+    const int ty = y / B.th, r = y - ty * B.th;
     if (r > 0 && !pixel_fg(B, d, y - 1, x)) return;   // same run of border cells, already linked
     const int lt = ty * d.TX + (right ? d.TX - 1 : 0);
     global_union(B.s.gp, edge_slot(B, d, lt, right ? RIGHT : LEFT, r), ext, ok);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
         if (t >= B.n_tiles) break;
         const ImgDesc &d = B.desc[sImg];
         const int nb = B.s.tstat[t].z;
-        const uint32_t slot0 = (uint32_t)(B.n_img + tile_geo(d, t - d.tile0).b);
+        const uint32_t slot0 = (uint32_t)(B.n_img + tile_geo(d, t - d.tile0, B.th).b);
         bool ok = true;
         int nfg = 0;
         for (int kb = threadIdx.x; kb < nb; kb += NTHREADS) {
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
         if (t >= B.n_tiles) break;
         const ImgDesc &d = B.desc[sImg];
         const int nb = B.s.tstat[t].z;
-        const uint32_t slot0 = (uint32_t)(B.n_img + tile_geo(d, t - d.tile0).b);
+        const uint32_t slot0 = (uint32_t)(B.n_img + tile_geo(d, t - d.tile0, B.th).b);
         for (int kb = threadIdx.x; kb < nb; kb += NTHREADS) {
             const uint32_t slot = slot0 + kb;
             const unsigned long long v = B.s.gp[slot];

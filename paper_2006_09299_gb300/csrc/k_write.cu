@@ -20,8 +20,14 @@ namespace ccl {
 
 constexpr uint32_t BOX_INIT = 0x3FFu;   // xmin = 1023, xmax = 0, ymax = 0
 
-constexpr size_t WRITE_SMEM = (size_t)MAXR * 8 + (size_t)MAXR * 4 + (size_t)MAXR * 4 +
-                              (size_t)NWARPS * TW * 4 + 3 * TH * WPR * 4 + 2 * TH * WPR * 2;
+// Local roots with on-chip feature records (more spill to global atomics).
+template <int TH>
+__host__ __device__ constexpr int maxr() { return TH == 32 ? 4096 : 2048; }
+
+template <int TH>
+constexpr size_t write_smem() {
+    return (size_t)maxr<TH>() * (8 + 4 + 4) + (size_t)NWARPS * TW * 4 + 3 * TH * WPR * 4 + 2 * TH * WPR * 2;
+}
 
 // Shared-memory box record of a local root: xmin | xmax << 10 | ymax << 20
 // (tile-local), updated by a compare-and-swap loop.
@@ -63,7 +69,9 @@ __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e)
     asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e) : "memory");
 }
 
-__global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
+template <int TH>
+__global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
+    constexpr int MAXR = maxr<TH>();
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *sSum = (unsigned long long *)smem;        // packed S | Sx << 16 | Sy << 41
     uint32_t *sBox = (uint32_t *)(sSum + MAXR);                   // xmin | xmax << 10 | ymax << 20
@@ -94,7 +102,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
         if (t >= B.n_tiles) break;
         const ImgDesc &d = B.desc[sImg];
         const int lt = t - d.tile0;
-        const TileGeo g = tile_geo(d, lt);
+        const TileGeo g = tile_geo(d, lt, TH);
         const int tx = g.tx, y0 = g.y0, x0 = g.x0, th = g.th, tw = g.tw;
         const int64_t rowwords = (int64_t)d.TX * WPR;
         const int64_t plane0 = (d.seg0 + (int64_t)y0 * d.TX + tx) * WPR;
@@ -134,7 +142,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
         __syncthreads();
         if (warp == 0) {
             int tot;
-            sRowRun[lane] = warp_excl_sum(sRowRun[lane], &tot);
+            const int ex = warp_excl_sum(lane < TH ? sRowRun[lane] : 0, &tot);
+            if (lane < TH) sRowRun[lane] = ex;
         }
         __syncthreads();
 
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
                 const int id = 1 + sRowSeg[0] + sNBPre[0][lane] + __popc(nb & mask_lt(b));
                 int p = 0;
                 if (y0 > 0) {
-                    const TileGeo ga = tile_geo(d, lt - d.TX);
+                    const TileGeo ga = tile_geo(d, lt - d.TX, TH);
                     const uint32_t s2 = (uint32_t)(n_img + ga.b) + B.s.edges[ga.b + edge_bottom(ga, c)];
                     const uint32_t root = (uint32_t)B.s.gp[s2];
                     p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
@@ -347,11 +356,17 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_write(Batch B) {
 }
 
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    k_write<<<min(B.n_tiles, 2 * c.sms), NTHREADS, WRITE_SMEM, st>>>(B);
+    if (B.th == 32)
+        k_write<32><<<min(B.n_tiles, 2 * c.sms), NTHREADS, write_smem<32>(), st>>>(B);
+    else
+        k_write<16><<<min(B.n_tiles, 3 * c.sms), NTHREADS, write_smem<16>(), st>>>(B);
 }
 
 cudaError_t configure_write() {
-    return cudaFuncSetAttribute(k_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WRITE_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_write<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)write_smem<32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_write<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)write_smem<16>());
+    return e;
 }
 
 }  // namespace ccl
