@@ -18,32 +18,24 @@
 
 namespace ccl {
 
-constexpr uint32_t BOX_INIT = 0x3FFu;   // xmin = 1023, xmax = 0, ymax = 0
 
 // Local roots with on-chip feature records (more spill to global atomics).
 template <int TH>
 __host__ __device__ constexpr int maxr() { return TH == 32 ? 4096 : 2048; }
 
+// Per local root: S, Sx, Sy, xmin, xmax, row mask (6 words, all updated
+// with native shared reductions) and the node id.
+constexpr int REC_WORDS = 6;
+
+// Threads per CTA: 32-row tiles run one 512-thread CTA per SM, 16-row
+// tiles two 256-thread CTAs (16 warps per SM either way).
+template <int TH>
+__host__ __device__ constexpr int write_threads() { return TH == 32 ? 512 : 256; }
+
 template <int TH>
 constexpr size_t write_smem() {
-    return (size_t)maxr<TH>() * (8 + 4 + 4) + (size_t)NWARPS * TW * 4 + 3 * TH * WPR * 4 + 2 * TH * WPR * 2;
-}
-
-// Shared-memory box record of a local root: xmin | xmax << 10 | ymax << 20
-// (tile-local), updated by a compare-and-swap loop.
-__device__ __forceinline__ bool box_update(uint32_t *p, int xs, int xl, int r) {
-    uint32_t old = *(volatile uint32_t *)p;
-    for (int it = 0; it < (1 << 16); ++it) {
-        const uint32_t nx0 = min(old & 1023u, (uint32_t)xs);
-        const uint32_t nx1 = max((old >> 10) & 1023u, (uint32_t)xl);
-        const uint32_t ny = max(old >> 20, (uint32_t)r);
-        const uint32_t nw = nx0 | (nx1 << 10) | (ny << 20);
-        if (nw == old) return true;
-        const uint32_t prev = atomicCAS(p, old, nw);
-        if (prev == old) return true;
-        old = prev;
-    }
-    return false;
+    return (size_t)maxr<TH>() * (REC_WORDS * 4 + 4) + (size_t)(write_threads<TH>() / 32) * TW * 4 +
+           3 * TH * WPR * 4 + 2 * TH * WPR * 2;
 }
 
 // Features of consecutive runs of one root on one row (tile-local x).
@@ -65,17 +57,47 @@ struct RunAcc {
     }
 };
 
+// Segmented inclusive scan over lanes (lane order = x order) of run
+// accumulators with equal roots; afterwards only the last lane of each group
+// of consecutive lanes with the same root keeps it (the others get k = -1).
+__device__ __forceinline__ void warp_combine(RunAcc &a, int lane) {
+    const int kprev = __shfl_up_sync(FULL, a.k, 1);
+    const bool head = lane == 0 || kprev != a.k;
+    int seg = head ? lane : 0;               // lane of this group's first member
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) seg = max(seg, __shfl_up_sync(FULL, seg, d));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t len = __shfl_up_sync(FULL, a.len, d), sx = __shfl_up_sync(FULL, a.sx, d);
+        const int x0 = __shfl_up_sync(FULL, a.x0, d);
+        if (lane - d >= seg) {
+            a.len += len;
+            a.sx += sx;
+            a.x0 = min(a.x0, x0);
+        }
+    }
+    const int knext = __shfl_down_sync(FULL, a.k, 1);
+    if (lane < 31 && knext == a.k) a.k = -1;   // not the group's last lane
+}
+
 __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e) {
     asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e) : "memory");
 }
 
 template <int TH>
-__global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
+__global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write(Batch B) {
     constexpr int MAXR = maxr<TH>();
+    constexpr int NTHREADS = write_threads<TH>();
+    constexpr int NWARPS = NTHREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long *sSum = (unsigned long long *)smem;        // packed S | Sx << 16 | Sy << 41
-    uint32_t *sBox = (uint32_t *)(sSum + MAXR);                   // xmin | xmax << 10 | ymax << 20
-    int32_t *sId = (int32_t *)(sBox + MAXR);                      // node id per local root
+    // feature records of the local roots, structure of arrays (tile-local x, y)
+    uint32_t *sArea = (uint32_t *)smem;
+    uint32_t *sSx = sArea + MAXR;
+    uint32_t *sSy = sSx + MAXR;
+    uint32_t *sX0 = sSy + MAXR;
+    uint32_t *sX1 = sX0 + MAXR;
+    uint32_t *sRows = sX1 + MAXR;                                 // bit r: a run on row r
+    int32_t *sId = (int32_t *)(sRows + MAXR);                     // node id per local root
     int32_t *sRid = sId + MAXR;                                   // per warp: node id per run of a row
     uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(sRid + NWARPS * TW);
     uint32_t(*sE)[WPR] = sC + TH;
@@ -164,8 +186,12 @@ __global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
             const int id = root_id(info);
             if (k < MAXR) {
                 sId[k] = id;
-                sSum[k] = 0ull;
-                sBox[k] = BOX_INIT;
+                sArea[k] = 0u;
+                sSx[k] = 0u;
+                sSy[k] = 0u;
+                sX0[k] = 0xFFFFu;
+                sX1[k] = 0u;
+                sRows[k] = 0u;
             } else if (!((info >> 17) & 1u) && id < cap) {
                 d.feat[0 * cap + id] = 0;
                 d.feat[1 * cap + id] = INT64_MAX;
@@ -203,9 +229,12 @@ __global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
                 auto flush = [&](const RunAcc &a) {
                     if (a.k < 0) return;
                     if (a.k < MAXR) {
-                        atomicAdd(&sSum[a.k], (unsigned long long)a.len | ((unsigned long long)a.sx << 16) |
-                                                  ((unsigned long long)(r * a.len) << 41));
-                        ok &= box_update(&sBox[a.k], a.x0, a.x1, r);
+                        atomicAdd(&sArea[a.k], a.len);      // results unused: reductions,
+                        atomicAdd(&sSx[a.k], a.sx);         // the lane does not wait
+                        atomicAdd(&sSy[a.k], (uint32_t)r * a.len);
+                        atomicMin(&sX0[a.k], (uint32_t)a.x0);
+                        atomicMax(&sX1[a.k], (uint32_t)a.x1);
+                        atomicOr(&sRows[a.k], 1u << r);
                     } else {
                         const int id = root_id(ri[a.k]);
                         if (id < cap)
@@ -228,6 +257,12 @@ __global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
                     }
                     ++q;
                 }
+                // the last accumulators of neighbouring lanes often hold the
+                // same root (a component crossing the row many times): combine
+                // equal roots of consecutive lanes, then the last lane of each
+                // group flushes
+                warp_combine(acc0, lane);
+                warp_combine(acc1, lane);
                 flush(acc0);
                 flush(acc1);
             }
@@ -322,13 +357,11 @@ __global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
             const bool isb = (info >> 17) & 1u;
             const int id = sId[k];
             if (id >= cap) continue;
-            const unsigned long long s = sSum[k];
-            const uint32_t bx = sBox[k];
-            const long long area = (long long)(s & 0xFFFFull);
-            const long long sx = (long long)((s >> 16) & ((1ull << 25) - 1)) + area * x0;
-            const long long sy = (long long)((s >> 41) & ((1ull << 20) - 1)) + area * y0;
-            const int xmin = x0 + (int)(bx & 1023u), xmax = x0 + (int)((bx >> 10) & 1023u);
-            const int ymax = y0 + (int)(bx >> 20), ymin = y0 + r;
+            const long long area = (long long)sArea[k];
+            const long long sx = (long long)sSx[k] + area * x0;
+            const long long sy = (long long)sSy[k] + area * y0;
+            const int xmin = x0 + (int)sX0[k], xmax = x0 + (int)sX1[k];
+            const int ymax = y0 + 31 - __clz(sRows[k]), ymin = y0 + r;
             if (!isb) {
                 d.feat[0 * cap + id] = area;
                 d.feat[1 * cap + id] = xmin;
@@ -357,9 +390,9 @@ __global__ void __launch_bounds__(NTHREADS, TH == 32 ? 2 : 3) k_write(Batch B) {
 
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     if (B.th == 32)
-        k_write<32><<<min(B.n_tiles, 2 * c.sms), NTHREADS, write_smem<32>(), st>>>(B);
+        k_write<32><<<min(B.n_tiles, c.sms), write_threads<32>(), write_smem<32>(), st>>>(B);
     else
-        k_write<16><<<min(B.n_tiles, 3 * c.sms), NTHREADS, write_smem<16>(), st>>>(B);
+        k_write<16><<<min(B.n_tiles, 2 * c.sms), write_threads<16>(), write_smem<16>(), st>>>(B);
 }
 
 cudaError_t configure_write() {
