@@ -113,46 +113,70 @@ __global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T) {
     }
 }
 
-// Absorbed nodes add their features to their survivor. Each thread first
-// sums consecutive contributions to the same survivor in registers (a
-// survivor absorbing many holes is met again and again by the same thread),
-// then goes through the CTA's hash table, then global atomics.
+// Absorbed nodes add their features to their survivor. A warp takes 32
+// consecutive node ids at a time (coalesced loads); consecutive absorbed
+// nodes usually share their survivor (the holes of one component are
+// numbered close together), so a segmented scan in lane order combines each
+// group of equal survivors and only the group's last lane pushes, through
+// the CTA's hash table, then global atomics.
 __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
     __shared__ __align__(16) unsigned char hmem[HT_BYTES];
     const HashTab H = hash_carve(hmem);
     hash_init(H);
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     const int64_t total = (int64_t)B.n_img + B.s.seg_base[B.n_segs];
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     ImageCursor cur;
-    int acc_img = -1, acc_id = -1;
-    FeatAcc acc{};
-    auto flush = [&]() {
-        if (acc_id >= 0) {
-            const ImgDesc &d = B.desc[acc_img];
-            hash_push(H, d.filled_feat, d.cap, acc_img, acc_id, acc);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < total;
+         base += warps * 32) {
+        const int64_t f = base + lane;
+        long long key = -1;   // (image << 32) | survivor, -1: nothing to add
+        FeatAcc v{0ull, 0ull, 0ull, INT32_MAX, INT32_MAX, -1, -1};
+        int img = 0;
+        if (f < total) {
+            cur.seek(B, f);
+            img = cur.img;
+            const ImgDesc &d = B.desc[img];
+            const int k = (int)(f - cur.lo);
+            if (d.fill_map != nullptr && k < min(d.cap, d.ncap)) {
+                const int s = d.fill_map[k];
+                if (s != k) {
+                    const int64_t cap = d.cap;
+                    key = ((long long)img << 32) | (uint32_t)s;
+                    v = FeatAcc{(unsigned long long)d.feat[0 * cap + k], (unsigned long long)d.feat[5 * cap + k],
+                                (unsigned long long)d.feat[6 * cap + k], (int)d.feat[1 * cap + k],
+                                (int)d.feat[2 * cap + k], (int)d.feat[3 * cap + k], (int)d.feat[4 * cap + k]};
+                }
+            }
         }
-    };
-    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
-        cur.seek(B, f);
-        const ImgDesc &d = B.desc[cur.img];
-        const int k = (int)(f - cur.lo);
-        if (d.fill_map == nullptr || k >= min(d.cap, d.ncap)) continue;
-        const int s = d.fill_map[k];
-        if (s == k) continue;
-        const int64_t cap = d.cap;
-        const FeatAcc v{(unsigned long long)d.feat[0 * cap + k], (unsigned long long)d.feat[5 * cap + k],
-                        (unsigned long long)d.feat[6 * cap + k], (int)d.feat[1 * cap + k],
-                        (int)d.feat[2 * cap + k], (int)d.feat[3 * cap + k], (int)d.feat[4 * cap + k]};
-        if (s == acc_id && cur.img == acc_img) {
-            acc_merge(acc, v);
-        } else {
-            flush();
-            acc_img = cur.img;
-            acc_id = s;
-            acc = v;
+        // segmented inclusive scan over lanes with equal keys
+        const long long kprev = __shfl_up_sync(FULL, key, 1);
+        int seg = (lane == 0 || kprev != key) ? lane : 0;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) seg = max(seg, __shfl_up_sync(FULL, seg, dd));
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const unsigned long long a = __shfl_up_sync(FULL, v.area, dd), sx = __shfl_up_sync(FULL, v.sx, dd),
+                                     sy = __shfl_up_sync(FULL, v.sy, dd);
+            const int x0 = __shfl_up_sync(FULL, v.xmin, dd), y0 = __shfl_up_sync(FULL, v.ymin, dd),
+                      x1 = __shfl_up_sync(FULL, v.xmax, dd), y1 = __shfl_up_sync(FULL, v.ymax, dd);
+            if (lane - dd >= seg) {
+                v.area += a;
+                v.sx += sx;
+                v.sy += sy;
+                v.xmin = min(v.xmin, x0);
+                v.ymin = min(v.ymin, y0);
+                v.xmax = max(v.xmax, x1);
+                v.ymax = max(v.ymax, y1);
+            }
+        }
+        const long long knext = __shfl_down_sync(FULL, key, 1);
+        if (key >= 0 && (lane == 31 || knext != key)) {
+            const ImgDesc &d = B.desc[img];
+            hash_push(H, d.filled_feat, d.cap, img, (int)(uint32_t)key, v);
         }
     }
-    flush();
     __syncthreads();
     hash_flush(H, B.desc, true);
 }

@@ -206,14 +206,34 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
 
         // ---- rows: run features, tree parents of the row below, label rows
         const bool labels = B.labels && d.fg != nullptr;
+        constexpr int PF = 4;
+        int pf[PF];
+        int pf_row = -1;
         for (int r = warp; r < th; r += NWARPS) {
             const uint32_t e = sE[r][lane];
             const int rowbase = sRowRun[r];
             const int nr = (r + 1 < TH ? sRowRun[r + 1] : st.x) - rowbase;
             int32_t *rid = sRid + warp * TW;
-            // root ordinals of the row's runs: one coalesced pass
-#pragma unroll 4
-            for (int i = lane; i < nr; i += 32) rid[swz(i)] = rr[rowbase + i];
+            // root ordinals of the row's runs: the first PF * 32 were fetched
+            // into registers while the warp worked on its previous row
+#pragma unroll
+            for (int j = 0; j < PF; ++j) {
+                const int i = lane + 32 * j;
+                if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[rowbase + i];
+            }
+            for (int i = lane + 32 * PF; i < nr; i += 32) rid[swz(i)] = rr[rowbase + i];
+            {
+                const int rn = r + NWARPS;   // this warp's next row
+                if (rn < th) {
+                    const int nb = sRowRun[rn], nn = (rn + 1 < TH ? sRowRun[rn + 1] : st.x) - nb;
+#pragma unroll
+                    for (int j = 0; j < PF; ++j) {
+                        const int i = lane + 32 * j;
+                        pf[j] = i < nn ? (int)rr[nb + i] : 0;
+                    }
+                    pf_row = rn;
+                }
+            }
             __syncwarp();
             // each lane walks the runs starting in its word. Along a row the
             // runs alternate colours, so a component crossing the row many
@@ -294,15 +314,27 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
                     if (x < tw) {
                         const int wl = x >> 5, b = x & 31;
                         const uint32_t ew = sE[r][wl], cw = sC[r][wl];
-                        const int p = sRunPre[r][wl] - 1;
+                        // run index of the group's first pixel, and run starts
+                        // inside the group (usually none: one lookup)
+                        const int q0 = sRunPre[r][wl] - 1 + __popc(ew & mask_le(b));
+                        const uint32_t s3 = (ew >> (b + 1)) & 7u, c4 = (cw >> b) & 15u;
+                        int id[4];
+                        id[0] = rid[swz(q0)];
+                        if (s3 == 0u) {
+                            id[1] = id[2] = id[3] = id[0];
+                        } else {
+                            const int q1 = q0 + (int)(s3 & 1u), q2 = q1 + (int)((s3 >> 1) & 1u),
+                                      q3 = q2 + (int)(s3 >> 2);
+                            id[1] = rid[swz(q1)];
+                            id[2] = rid[swz(q2)];
+                            id[3] = rid[swz(q3)];
+                        }
                         int fv[4], bv[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const int bit = b + j;
-                            const int id = rid[swz(p + __popc(ew & mask_le(bit)))];
-                            const bool isfg = (cw >> bit) & 1u;
-                            fv[j] = isfg ? id : -1;
-                            bv[j] = isfg ? -1 : id;
+                            const bool isfg = (c4 >> j) & 1u;
+                            fv[j] = isfg ? id[j] : -1;
+                            bv[j] = isfg ? -1 : id[j];
                         }
                         if (d.vec) {
                             st_cs_v4(fgrow + x, fv[0], fv[1], fv[2], fv[3]);
