@@ -202,30 +202,38 @@ int oracle_analyze(const uint8_t *img, int32_t w, int32_t h, int32_t pitch,
 }
 
 /*
- * Hole filling with an area threshold (Algorithm 3, hole-filling branch: a
- * root whose surrounding component is not the exterior is made equivalent to
- * it; here a background component is absorbed only when its own area is at
- * most T). Nodes are visited in increasing order, so a parent is settled
- * before its children (parent[n] < n).
- *   hole(n)  = n is background, n != 0 and area[n] <= T   (T < 0: no hole)
- *   map[n]   = map[parent[n]] if hole(n), or if n is foreground and
- *              hole(parent[n]); otherwise n.
+ * Component filtering by area, the connected operator the paper applies to
+ * holes (Algorithm 3, hole-filling branch: a root whose surrounding
+ * component is not the exterior is made equivalent to it) and names for
+ * other features (Section 5). target_fg = 0 fills holes: a background
+ * component other than the exterior is absorbed by its parent when its own
+ * area is at most T. target_fg = 1 removes small objects the same way: a
+ * foreground component with area at most T is absorbed by its parent
+ * background component. Either way the children of an absorbed component
+ * (of the other colour) are absorbed with it. Nodes are visited in
+ * increasing order, so a parent is settled before its children
+ * (parent[n] < n).
+ *   target(n) = colour(n) == target_fg, n != 0 and area[n] <= T  (T < 0: none)
+ *   map[n]    = map[parent[n]] if target(n), or if colour(n) != target_fg,
+ *               n != 0 and target(parent[n]); otherwise n.
  * Survivors (map[s] == s) get the merge (sum / min / max) of the features of
  * all nodes mapped to them; absorbed nodes get the empty-component features.
  * filled_parent[s] = map[parent[s]] for survivors (-1 for node 0), and -1 for
  * absorbed nodes. The tree passed in is not modified.
  */
-int oracle_fill(int32_t n_nodes, const int32_t *parent, const int64_t *feat,
-                int64_t cap, const uint8_t *node_fg, int64_t T, int32_t *map,
-                int64_t *ffeat, int64_t fcap, int32_t *fparent)
+int oracle_filter(int32_t n_nodes, const int32_t *parent, const int64_t *feat,
+                  int64_t cap, const uint8_t *node_fg, int32_t target_fg, int64_t T,
+                  int32_t *map, int64_t *ffeat, int64_t fcap, int32_t *fparent)
 {
     if (n_nodes < 1 || n_nodes > cap || n_nodes > fcap) return OR_ERR_ARG;
+    if (target_fg != 0 && target_fg != 1) return OR_ERR_ARG;
     uint8_t *hole = (uint8_t *)malloc((size_t)n_nodes);
     if (!hole) return OR_ERR_OOM;
     for (int32_t n = 0; n < n_nodes; ++n) {
-        hole[n] = (uint8_t)(T >= 0 && n != 0 && !node_fg[n] &&
+        const int is_target_colour = (node_fg[n] != 0) == (target_fg != 0);
+        hole[n] = (uint8_t)(T >= 0 && n != 0 && is_target_colour &&
                             feat[OR_AREA * cap + n] <= T);
-        if (hole[n] || (n != 0 && node_fg[n] && hole[parent[n]]))
+        if (hole[n] || (n != 0 && !is_target_colour && hole[parent[n]]))
             map[n] = map[parent[n]];
         else
             map[n] = n;
@@ -261,4 +269,13 @@ int oracle_fill(int32_t n_nodes, const int32_t *parent, const int64_t *feat,
     }
     free(hole);
     return OR_OK;
+}
+
+/* Hole filling: the filter with background as the target colour. */
+int oracle_fill(int32_t n_nodes, const int32_t *parent, const int64_t *feat,
+                int64_t cap, const uint8_t *node_fg, int64_t T, int32_t *map,
+                int64_t *ffeat, int64_t fcap, int32_t *fparent)
+{
+    return oracle_filter(n_nodes, parent, feat, cap, node_fg, 0, T, map, ffeat,
+                         fcap, fparent);
 }

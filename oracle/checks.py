@@ -72,3 +72,16 @@ def brute_fill_image(img01, node, colour_of, area, T):
         mask = np.isin(node, np.asarray(holes))
         img[mask] = 1
     return img
+
+
+def brute_remove_objects(img01, node, colour_of, area, T):
+    """Paint every foreground node with area <= T background; return the new
+    0/1 image."""
+    img = (np.asarray(img01) != 0).astype(np.uint8)
+    node = np.asarray(node)
+    if T < 0:
+        return img
+    objs = [k for k in range(1, len(colour_of)) if colour_of[k] and area[k] <= T]
+    if objs:
+        img[np.isin(node, np.asarray(objs))] = 0
+    return img

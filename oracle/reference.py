@@ -42,6 +42,8 @@ def _load():
         lib.oracle_analyze.restype = ctypes.c_int
         lib.oracle_fill.argtypes = [i32, p, p, i64, p, i64, p, p, i64, p]
         lib.oracle_fill.restype = ctypes.c_int
+        lib.oracle_filter.argtypes = [i32, p, p, i64, p, i32, i64, p, p, i64, p]
+        lib.oracle_filter.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -85,10 +87,11 @@ def analyze(img, w=None, conn=0, cap=None):
                 node_fg=node_fg[:n].copy(), counts=counts, n=n, w=w, h=h)
 
 
-def fill(res, T):
-    """Hole filling with area threshold T on an analyze() result.
+def fill(res, T, target_fg=0):
+    """Area filter on an analyze() result: target_fg = 0 fills holes with
+    area <= T, target_fg = 1 removes foreground objects with area <= T.
 
-    Returns (map [N], filled_feat [7][N], filled_parent [N])."""
+    Returns (map [N], filtered_feat [7][N], filtered_parent [N])."""
     lib = _load()
     n = res["n"]
     parent = np.ascontiguousarray(res["parent"], np.int32)
@@ -97,11 +100,19 @@ def fill(res, T):
     fmap = np.empty(n, np.int32)
     ffeat = np.empty((NF, n), np.int64)
     fpar = np.empty(n, np.int32)
-    rc = lib.oracle_fill(n, _ptr(parent), _ptr(feat), n, _ptr(node_fg), int(T), _ptr(fmap),
-                         _ptr(ffeat), n, _ptr(fpar))
+    rc = lib.oracle_filter(n, _ptr(parent), _ptr(feat), n, _ptr(node_fg), int(target_fg), int(T), _ptr(fmap),
+                           _ptr(ffeat), n, _ptr(fpar))
     if rc != 0:
-        raise RuntimeError("oracle_fill failed with status %d" % rc)
+        raise RuntimeError("oracle_filter failed with status %d" % rc)
     return fmap, ffeat, fpar
+
+
+def relabel(res, fmap):
+    """Label images after filtering: every pixel takes the survivor of its
+    node, in the label image of the survivor's colour (-1 in the other)."""
+    s = fmap[res["node"]]
+    col = res["node_fg"][s].astype(bool)
+    return np.where(col, s, -1).astype(np.int32), np.where(col, -1, s).astype(np.int32)
 
 
 def euler(res):

@@ -91,20 +91,20 @@ def analyze(rows, conn=0):
                 first=first, n=n, counts=[n, n_fg, n - n_fg, 0])
 
 
-def fill(res, T):
-    """Hole filling with area threshold T, stated as: a node is absorbed when
-    it is a hole (background, not node 0, area <= T) or a foreground child of
-    such a hole; every node maps to its nearest ancestor-or-self that is not
-    absorbed. Returns (map, filled features, filled parent)."""
+def fill(res, T, target_fg=0):
+    """Area filter, stated as: a node is absorbed when it is a target (colour
+    target_fg, not node 0, area <= T: a hole when target_fg = 0, an object
+    when 1) or a child of a target; every node maps to its nearest
+    ancestor-or-self that is not absorbed. Returns (map, features, parent)."""
     n = res["n"]
     parent = res["parent"]
     colour = res["colour"]
     feat = res["feat"]
 
-    def is_hole(k):
-        return T >= 0 and k != 0 and not colour[k] and feat[k][0] <= T
+    def is_target(k):
+        return T >= 0 and k != 0 and colour[k] == target_fg and feat[k][0] <= T
 
-    absorbed = [is_hole(k) or (k != 0 and colour[k] and is_hole(parent[k])) for k in range(n)]
+    absorbed = [is_target(k) or (k != 0 and colour[k] != target_fg and is_target(parent[k])) for k in range(n)]
     fmap = []
     for k in range(n):
         s = k

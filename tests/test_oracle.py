@@ -352,3 +352,45 @@ def test_capacity_bound_reached():
         img[:, 0] = img[:, -1] = 1
         res = orc.analyze(img)
         assert res["n"] <= orc.capacity(w, h)
+
+
+# --------------------------------------------------- object removal (dual)
+
+
+@pytest.mark.parametrize("T", [-1, 0, 1, 2, 4, 9, 30, INT64_MAX])
+def test_object_removal_matches_brute_force(T):
+    """Removing foreground objects with area <= T from the node table equals
+    painting them background and labelling again."""
+    rng = np.random.default_rng(41)
+    for it in range(40):
+        h, w = int(rng.integers(2, 40)), int(rng.integers(2, 40))
+        img = inputs.granular(h, w, float(rng.uniform(0.2, 0.7)), int(rng.integers(1, 3)), it + 100)
+        res = orc.analyze(img)
+        fmap, ff, fpar = orc.fill(res, T, target_fg=1)
+        painted = checks.brute_remove_objects(img, res["node"], res["node_fg"], res["feat"][orc.AREA], T)
+        res2 = orc.analyze(painted)
+        pairs = set(zip(fmap[res["node"]].ravel().tolist(), res2["node"].ravel().tolist()))
+        assert len(pairs) == len({a for a, _ in pairs}) == len({b for _, b in pairs})
+        for a, b in pairs:
+            assert list(ff[:, a]) == list(res2["feat"][:, b])
+        # the relabelled images equal the repainted image's labels up to renumbering
+        fg2, bg2 = orc.relabel(res, fmap)
+        assert np.array_equal(fg2 >= 0, painted != 0) and np.array_equal(bg2 >= 0, painted == 0)
+        for k in range(res["n"]):
+            if fmap[k] != k:
+                assert fpar[k] == -1 and ff[orc.AREA, k] == 0
+
+
+def test_filters_match_twin():
+    rng = np.random.default_rng(43)
+    for it in range(150):
+        h, w = int(rng.integers(1, 11)), int(rng.integers(1, 11))
+        img = (rng.random((h, w)) < rng.uniform(0.2, 0.8)).astype(np.uint8)
+        res = orc.analyze(img)
+        tw = twin.analyze(img.tolist())
+        for tgt in (0, 1):
+            for T in (-1, 0, 1, 3, INT64_MAX):
+                fmap, ff, fpar = orc.fill(res, T, target_fg=tgt)
+                m2, f2, p2 = twin.fill(tw, T, target_fg=tgt)
+                assert list(fmap) == m2 and list(fpar) == p2
+                assert ff.T.tolist() == f2
