@@ -139,10 +139,36 @@ ccl_status ccl_fill_holes(ccl_ctx *ctx, int64_t area_threshold, int32_t *d_fill_
                           int64_t *d_filled_features, int32_t *d_filled_parent,
                           ccl_stream_t stream);
 
+/* Area filter on either colour, the connected operator of which hole filling
+ * is one case (Algorithm 3, hole-filling branch; Section 5 names filtering
+ * components on their features as the general form):
+ *   CCL_TARGET_HOLES    background nodes other than 0 with area <= T are
+ *                       absorbed by their parent (exactly ccl_fill_holes);
+ *   CCL_TARGET_OBJECTS  foreground nodes with area <= T are absorbed by their
+ *                       parent background node (small objects removed).
+ * The children of an absorbed node (other colour) are absorbed with it.
+ * Outputs and rules otherwise as for ccl_fill_holes. */
+enum { CCL_TARGET_HOLES = 0, CCL_TARGET_OBJECTS = 1 };
+ccl_status ccl_filter_components(ccl_ctx *ctx, int32_t target, int64_t area_threshold, int32_t *d_map,
+                                 int64_t *d_features, int32_t *d_parent, ccl_stream_t stream);
+
+/* Label images after the last fill / filter of this context (Algorithm 4
+ * applied to the filtered equivalence table): every pixel of node n takes
+ * map[n], in d_fg_out when that survivor is foreground and in d_bg_out
+ * otherwise (-1 in the other image). Reads the label images of the last
+ * ccl_analyze; the outputs may be those same buffers (in place).
+ * CCL_ERR_STATE if the last analyze wrote no label images or no fill ran. */
+ccl_status ccl_relabel_filtered(ccl_ctx *ctx, int32_t *d_fg_out, int32_t *d_bg_out, ccl_stream_t stream);
+
 /* Wait for the stream of the last call and read that call's counts (any
  * pointer may be NULL). Returns the OR of the device status bits of the last
  * analyze / fill (CCL_OK when clean). */
 ccl_status ccl_get_counts(ccl_ctx *ctx, int32_t *n_nodes, int32_t *n_fg, int32_t *n_bg);
+
+/* Euler number of the last analysed image (waits like ccl_get_counts): the
+ * number of foreground components minus the number of holes, n_fg - (n_bg - 1)
+ * (the paper lists it among the computed features, Sections 1 and 4). */
+ccl_status ccl_get_euler(ccl_ctx *ctx, int64_t *euler);
 
 /* ---------------------------------------------------------------- batches */
 
@@ -181,6 +207,11 @@ ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, i
 
 /* Hole filling for every image of the last batch that has fill buffers. */
 ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stream_t stream);
+
+/* Area filter (ccl_filter_components) for every image of the last batch
+ * that has fill buffers. */
+ccl_status ccl_filter_components_batched(ccl_ctx *ctx, int32_t target, int64_t area_threshold,
+                                         ccl_stream_t stream);
 
 /* Tile height for later analyses of this context: 32 rows (default) or 16
  * rows of 1024 columns. Results are identical; the speed differs with the

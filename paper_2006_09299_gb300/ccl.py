@@ -21,6 +21,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_ALIGN, ERR_CAPACITY, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT, ERR_STATE = 0, 1, 2, 4, 8, 16, 32, 64
 F_AREA, F_XMIN, F_YMIN, F_XMAX, F_YMAX, F_SX, F_SY, F_COUNT = range(8)
 CONN_8FG_4BG, CONN_4FG_8BG = 0, 1
+TARGET_HOLES, TARGET_OBJECTS = 0, 1
 INT64_MAX = (1 << 63) - 1
 
 _p = ctypes.c_void_p
@@ -43,6 +44,10 @@ SIGNATURES = {
     "ccl_set_connectivity": (ctypes.c_int, [_p, _i32]),
     "ccl_analyze": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "ccl_fill_holes": (ctypes.c_int, [_p, _i64, _p, _p, _p, _p]),
+    "ccl_filter_components": (ctypes.c_int, [_p, _i32, _i64, _p, _p, _p, _p]),
+    "ccl_relabel_filtered": (ctypes.c_int, [_p, _p, _p, _p]),
+    "ccl_get_euler": (ctypes.c_int, [_p, ctypes.POINTER(_i64)]),
+    "ccl_filter_components_batched": (ctypes.c_int, [_p, _i32, _i64, _p]),
     "ccl_get_counts": (ctypes.c_int, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "ccl_create_batched": (ctypes.c_int, [ctypes.POINTER(_p), _i32, _i64, _i32]),
     "ccl_analyze_batched": (ctypes.c_int, [_p, ctypes.POINTER(ImageDesc), _i32, _p]),
@@ -184,6 +189,27 @@ class Context(_Instrumented):
                "ccl_fill_holes")
         return out
 
+    def filter_components(self, target, area_threshold, out=None, stream=None):
+        """Area filter on the last analyze (TARGET_HOLES or TARGET_OBJECTS)."""
+        if out is None:
+            out = self.last.alloc_fill() if self.last.fill_map is None else self.last
+        _check(_lib.ccl_filter_components(self._h, int(target), int(area_threshold), _ptr(out.fill_map),
+                                          _ptr(out.filled_features), _ptr(out.filled_parent), _stream(stream)),
+               "ccl_filter_components")
+        return out
+
+    def relabel_filtered(self, fg_out, bg_out, stream=None):
+        """Label images through the map of the last fill / filter."""
+        _check(_lib.ccl_relabel_filtered(self._h, _ptr(fg_out), _ptr(bg_out), _stream(stream)),
+               "ccl_relabel_filtered")
+
+    def euler(self):
+        e = _i64()
+        st = _lib.ccl_get_euler(self._h, ctypes.byref(e))
+        if st not in (OK, ERR_CAPACITY):
+            raise CCLError(st, "ccl_get_euler")
+        return e.value
+
     def get_counts(self):
         n, nf, nb = _i32(), _i32(), _i32()
         st = _lib.ccl_get_counts(self._h, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nb))
@@ -234,6 +260,10 @@ class BatchContext(_Instrumented):
     def fill_holes(self, area_threshold, stream=None):
         _check(_lib.ccl_fill_holes_batched(self._h, int(area_threshold), _stream(stream)),
                "ccl_fill_holes_batched")
+
+    def filter_components(self, target, area_threshold, stream=None):
+        _check(_lib.ccl_filter_components_batched(self._h, int(target), int(area_threshold), _stream(stream)),
+               "ccl_filter_components_batched")
 
     def close(self):
         if self._h:

@@ -427,27 +427,58 @@ ccl_status ccl_analyze(ccl_ctx *ctx, const uint8_t *d_img, int32_t *d_fg_labels,
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
 
-static ccl_status fill_last(ccl_ctx *ctx, int64_t T, cudaStream_t st) {
+static ccl_status fill_last(ccl_ctx *ctx, int64_t T, int32_t target, cudaStream_t st) {
     const Plan &P = ctx->last;
     cudaError_t e = upload_plan(ctx, P, st);
     if (e != cudaSuccess) return CCL_ERR_CUDA;
-    launch_fill(make_batch(ctx, P), T, LaunchCfg{g_sms}, st, timing_slot(ctx, 1));
+    launch_fill(make_batch(ctx, P), T, target, LaunchCfg{g_sms}, st, timing_slot(ctx, 1));
     e = cudaGetLastError();
     ctx->launches += FILL_KERNELS;
     ctx->last_stream = st;
     return from_cuda(e);
 }
 
-ccl_status ccl_fill_holes(ccl_ctx *ctx, int64_t area_threshold, int32_t *d_fill_map, int64_t *d_filled_features,
-                          int32_t *d_filled_parent, ccl_stream_t stream) {
+ccl_status ccl_filter_components(ccl_ctx *ctx, int32_t target, int64_t area_threshold, int32_t *d_map,
+                                 int64_t *d_features, int32_t *d_parent, ccl_stream_t stream) {
     if (!ctx || ctx->batched) return CCL_ERR_ARG;
-    if (!d_fill_map || !d_filled_features || !d_filled_parent) return CCL_ERR_ARG;
+    if (target != CCL_TARGET_HOLES && target != CCL_TARGET_OBJECTS) return CCL_ERR_ARG;
+    if (!d_map || !d_features || !d_parent) return CCL_ERR_ARG;
     if (!ctx->have_last) return CCL_ERR_STATE;
     ImgDesc &d = ctx->last.d[0];
-    d.fill_map = d_fill_map;
-    d.filled_feat = d_filled_features;
-    d.filled_parent = d_filled_parent;
-    return fill_last(ctx, area_threshold, (cudaStream_t)stream);
+    d.fill_map = d_map;
+    d.filled_feat = d_features;
+    d.filled_parent = d_parent;
+    return fill_last(ctx, area_threshold, target, (cudaStream_t)stream);
+}
+
+ccl_status ccl_fill_holes(ccl_ctx *ctx, int64_t area_threshold, int32_t *d_fill_map, int64_t *d_filled_features,
+                          int32_t *d_filled_parent, ccl_stream_t stream) {
+    return ccl_filter_components(ctx, CCL_TARGET_HOLES, area_threshold, d_fill_map, d_filled_features,
+                                 d_filled_parent, stream);
+}
+
+ccl_status ccl_relabel_filtered(ccl_ctx *ctx, int32_t *d_fg_out, int32_t *d_bg_out, ccl_stream_t stream) {
+    if (!ctx || ctx->batched || !d_fg_out || !d_bg_out) return CCL_ERR_ARG;
+    if (!ctx->have_last || !ctx->last.d[0].fill_map || !ctx->last.d[0].fg) return CCL_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan P = ctx->last;
+    P.d[0].fg_out = d_fg_out;
+    P.d[0].bg_out = d_bg_out;
+    cudaError_t e = upload_plan(ctx, P, st);
+    if (e != cudaSuccess) return CCL_ERR_CUDA;
+    launch_relabel(make_batch(ctx, P), LaunchCfg{g_sms}, st);
+    ctx->launches += 1;
+    ctx->last_stream = st;
+    return from_cuda(cudaGetLastError());
+}
+
+ccl_status ccl_get_euler(ccl_ctx *ctx, int64_t *euler) {
+    if (!ctx || !euler) return CCL_ERR_ARG;
+    int32_t n = 0, nf = 0, nb = 0;
+    const ccl_status st = ccl_get_counts(ctx, &n, &nf, &nb);
+    if (st != CCL_OK && st != CCL_ERR_CAPACITY) return st;
+    *euler = (int64_t)nf - ((int64_t)nb - 1);
+    return st;
 }
 
 ccl_status ccl_get_counts(ccl_ctx *ctx, int32_t *n_nodes, int32_t *n_fg, int32_t *n_bg) {
@@ -490,10 +521,16 @@ ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, i
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
 
-ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stream_t stream) {
+ccl_status ccl_filter_components_batched(ccl_ctx *ctx, int32_t target, int64_t area_threshold,
+                                         ccl_stream_t stream) {
     if (!ctx || !ctx->batched) return CCL_ERR_ARG;
+    if (target != CCL_TARGET_HOLES && target != CCL_TARGET_OBJECTS) return CCL_ERR_ARG;
     if (!ctx->have_last) return CCL_ERR_STATE;
-    return fill_last(ctx, area_threshold, (cudaStream_t)stream);
+    return fill_last(ctx, area_threshold, target, (cudaStream_t)stream);
+}
+
+ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stream_t stream) {
+    return ccl_filter_components_batched(ctx, CCL_TARGET_HOLES, area_threshold, stream);
 }
 
 ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows) {

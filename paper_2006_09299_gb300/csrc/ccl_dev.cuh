@@ -54,6 +54,7 @@ struct ImgDesc {
     int32_t *fill_map;         // [cap] or null
     int64_t *filled_feat;      // [7][cap]
     int32_t *filled_parent;    // [cap]
+    int32_t *fg_out, *bg_out;  // label images rewritten through fill_map (or null)
     int32_t w, h, pitch;
     int32_t TX, TY;            // tiles across and down
     int32_t tile0;             // first flat tile of the image
@@ -408,8 +409,9 @@ void launch_resolve(const Batch &B, const LaunchCfg &c, cudaStream_t st);
 void launch_scan(const Batch &B, cudaStream_t st);
 void launch_canon(const Batch &B, const LaunchCfg &c, cudaStream_t st);
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st);
-void launch_fill(const Batch &B, int64_t area_threshold, const LaunchCfg &c, cudaStream_t st,
+void launch_fill(const Batch &B, int64_t area_threshold, int32_t target_fg, const LaunchCfg &c, cudaStream_t st,
                  const cudaEvent_t *ev = nullptr);
+void launch_relabel(const Batch &B, const LaunchCfg &c, cudaStream_t st);
 cudaError_t configure_label();
 cudaError_t configure_write();
 

@@ -1,20 +1,26 @@
-// Hole filling on the node tables (the paper's Algorithm 3, hole-filling
-// branch: a root whose surrounding component is not the exterior becomes
-// equivalent to it, and its features merge into it; no pixel is rescanned).
+// Component filtering on the node tables: the paper's hole filling
+// (Algorithm 3, hole-filling branch: a root whose surrounding component is
+// not the exterior becomes equivalent to it, and its features merge into it;
+// no pixel is rescanned) with an area threshold, and its dual for the other
+// colour, the feature-based connected operator Section 5 names.
 //
-// Extended with an area threshold T: a hole (background node other than 0)
-// is absorbed when its own area is <= T, and so is every foreground child of
-// an absorbed hole. Every node maps to its nearest ancestor-or-self that is
-// not absorbed. T < 0 absorbs nothing; T = INT64_MAX absorbs every hole and
-// reproduces the unconditional fill of Algorithm 3.
+// Target colour background (hole filling): a hole (background node other
+// than 0) is absorbed when its own area is <= T, and so is every foreground
+// child of an absorbed hole. Target colour foreground (object removal): a
+// foreground node with area <= T is absorbed by its parent background node,
+// with its background children. Every node maps to its nearest
+// ancestor-or-self that is not absorbed. T < 0 absorbs nothing; hole filling
+// with T = INT64_MAX is exactly the unconditional fill of Algorithm 3.
 //
 //   k_fill_map    map, survivor features copied, parents of survivors
 //   k_fill_merge  features of absorbed nodes merged into their survivor
+//   k_relabel     label images rewritten through the map (Algorithm 4 on
+//                 the filtered equivalence table)
 //
-// Both kernels walk one flat index over the nodes of every image of the last
-// analysis: image i's nodes start at i + seg_base[first segment of i], since
-// the node scan runs across all images in order and each image adds its
-// exterior node.
+// The node kernels walk one flat index over the nodes of every image of the
+// last analysis: image i's nodes start at i + seg_base[first segment of i],
+// since the node scan runs across all images in order and each image adds
+// its exterior node.
 #include "ccl_dev.cuh"
 
 namespace ccl {
@@ -26,24 +32,25 @@ struct FillView {
     const int64_t *area;
     const uint8_t *fg;
     int64_t T;
+    int32_t target;   // colour of the components that can be absorbed
 };
 
-__device__ __forceinline__ bool is_hole(const FillView &v, int m) {
-    return v.T >= 0 && m != 0 && !v.fg[m] && v.area[m] <= v.T;
+__device__ __forceinline__ bool is_target(const FillView &v, int m) {
+    return v.T >= 0 && m != 0 && (int)v.fg[m] == v.target && v.area[m] <= v.T;
 }
 
 // Every node m > 0 has 0 <= parent[m] < m; a value outside that range is
 // reported (CCL_ERR_ITER_LIMIT) and the walk stops instead of reading it.
 __device__ __forceinline__ bool absorbed(const FillView &v, int m, bool *ok) {
     if (m == 0) return false;
-    if (is_hole(v, m)) return true;
-    if (!v.fg[m]) return false;
+    if (is_target(v, m)) return true;
+    if ((int)v.fg[m] == v.target) return false;
     const int p = v.parent[m];
     if (p < 0 || p >= m) {
         *ok = false;
         return false;
     }
-    return is_hole(v, p);
+    return is_target(v, p);
 }
 
 __device__ __forceinline__ int survivor(const FillView &v, int m, bool *ok) {
@@ -81,7 +88,7 @@ struct ImageCursor {
     }
 };
 
-__global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T) {
+__global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T, int32_t target) {
     const int64_t total = (int64_t)B.n_img + B.s.seg_base[B.n_segs];
     ImageCursor cur;
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T) {
         const ImgDesc &d = B.desc[cur.img];
         const int k = (int)(f - cur.lo);
         if (d.fill_map == nullptr || k >= min(d.cap, d.ncap)) continue;
-        const FillView v{d.parent, d.feat, B.s.node_fg + d.node0, T};
+        const FillView v{d.parent, d.feat, B.s.node_fg + d.node0, T, target};
         const int64_t cap = d.cap;
         bool ok = true;
         const int s = survivor(v, k, &ok);
@@ -181,13 +188,46 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
     hash_flush(H, B.desc, true);
 }
 
-void launch_fill(const Batch &B, int64_t T, const LaunchCfg &c, cudaStream_t st, const cudaEvent_t *ev) {
+// Label images through the map: a pixel of node n takes map[n], in the
+// label image of the survivor's colour (-1 in the other). In place is fine
+// (each pixel is read before it is written, by the same thread).
+__global__ void __launch_bounds__(256) k_relabel(Batch B) {
+    const ImgDesc &d = B.desc[blockIdx.y];
+    if (d.fill_map == nullptr || d.fg == nullptr || d.fg_out == nullptr) return;
+    const int64_t npx = (int64_t)d.w * d.h;
+    const int n = min((int64_t)d.counts[0], min(d.cap, d.ncap));
+    const uint8_t *col = B.s.node_fg + d.node0;
+    bool ok = true;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npx; i += (int64_t)gridDim.x * blockDim.x) {
+        const int f = d.fg[i], g = d.bg[i];
+        const int node = f >= 0 ? f : g;
+        int s = node, c = 0;
+        if (node >= 0 && node < n) s = d.fill_map[node];
+        if (s >= 0 && s < n) {
+            c = col[s];
+        } else {
+            ok = false;
+            s = -1;
+        }
+        d.fg_out[i] = c ? s : -1;
+        d.bg_out[i] = c ? -1 : s;
+    }
+    if (!ok) set_status(B, d, ST_CAPACITY);
+}
+
+void launch_fill(const Batch &B, int64_t T, int32_t target, const LaunchCfg &c, cudaStream_t st,
+                 const cudaEvent_t *ev) {
     const int grid = 8 * c.sms;
     if (ev) cudaEventRecord(ev[0], st);
-    k_fill_map<<<grid, 256, 0, st>>>(B, T);
+    k_fill_map<<<grid, 256, 0, st>>>(B, T, target);
     if (ev) cudaEventRecord(ev[1], st);
     k_fill_merge<<<grid, 256, 0, st>>>(B);
     if (ev) cudaEventRecord(ev[2], st);
+}
+
+void launch_relabel(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
+    const dim3 grid(max(1, (8 * c.sms + B.n_img - 1) / B.n_img), B.n_img);
+    k_relabel<<<grid, 256, 0, st>>>(B);
 }
 
 }  // namespace ccl

@@ -206,3 +206,62 @@ def test_rings_8192_full(ccl):
     img = inputs.rings()
     g = run_single(ccl, img, 8192, fills=(64,))
     assert_parity(g, run_oracle(img, 8192), fills=(64,))
+
+
+@pytest.mark.parametrize("conn", [0, 1])
+def test_filter_objects_relabel_euler(ccl, conn):
+    """Small-object removal (the dual filter), the label images rewritten
+    through the filter map, and the Euler number, each against the oracle and
+    against the pixel-level brute force of the oracle's checks."""
+    from oracle import checks
+    for seed, (h, w) in enumerate([(1, 1), (33, 1023), (70, 2049), (257, 1100)]):
+        img = inputs.granular(h, w, 0.45, 1 + seed % 3, 11 + seed)
+        pitch = -(-w // 16) * 16
+        padded = np.zeros((h, pitch), np.uint8)
+        padded[:, :w] = img
+        r = run_oracle(padded, w, conn)
+        ctx = ccl.Context(w, h, pitch, conn=conn)
+        out = ctx.analyze(to_dev(padded))
+        n = ctx.get_counts()[0]
+        assert ctx.euler() == orc.euler(r) == checks.euler_bitquad(padded[:, :w], conn)
+        for target, T in ((ccl.TARGET_OBJECTS, 3), (ccl.TARGET_OBJECTS, 40), (ccl.TARGET_HOLES, 5)):
+            ctx.filter_components(target, T)
+            fg_out = torch.empty_like(out.fg)
+            bg_out = torch.empty_like(out.bg)
+            ctx.relabel_filtered(fg_out, bg_out)
+            torch.cuda.synchronize()
+            assert ctx.get_counts()[3] == 0
+            fmap, ff, fpar = orc.fill(r, T, target_fg=target)
+            np.testing.assert_array_equal(out.fill_map[:n].cpu().numpy(), fmap)
+            np.testing.assert_array_equal(out.filled_features[:, :n].cpu().numpy(), ff)
+            np.testing.assert_array_equal(out.filled_parent[:n].cpu().numpy(), fpar)
+            efg, ebg = orc.relabel(r, fmap)
+            np.testing.assert_array_equal(fg_out.cpu().numpy(), efg)
+            np.testing.assert_array_equal(bg_out.cpu().numpy(), ebg)
+        # in place: the outputs may be the analysis label images themselves
+        ctx.filter_components(ccl.TARGET_OBJECTS, 3)
+        ctx.relabel_filtered(out.fg, out.bg)
+        torch.cuda.synchronize()
+        efg, ebg = orc.relabel(r, orc.fill(r, 3, target_fg=1)[0])
+        np.testing.assert_array_equal(out.fg.cpu().numpy(), efg)
+        np.testing.assert_array_equal(out.bg.cpu().numpy(), ebg)
+        ctx.close()
+
+
+def test_filter_batched_objects(ccl):
+    batch = inputs.uneven_batch(seed=9, n=12, lo=16, hi=1200)
+    imgs = [(to_dev(p), w) for p, w in batch]
+    tot = sum(p.shape[0] * w for p, w in batch)
+    bctx = ccl.BatchContext(len(batch), tot, 1200)
+    outs = bctx.analyze(imgs, fill=True)
+    bctx.filter_components(ccl.TARGET_OBJECTS, 12)
+    torch.cuda.synchronize()
+    for (p, w), o in zip(batch, outs):
+        r = run_oracle(p, w)
+        n = o.n
+        assert o.status() == 0 and n == r["n"]
+        fmap, ff, fpar = orc.fill(r, 12, target_fg=1)
+        np.testing.assert_array_equal(o.fill_map[:n].cpu().numpy(), fmap)
+        np.testing.assert_array_equal(o.filled_features[:, :n].cpu().numpy(), ff)
+        np.testing.assert_array_equal(o.filled_parent[:n].cpu().numpy(), fpar)
+    bctx.close()
