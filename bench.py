@@ -8,7 +8,10 @@ int64 features) followed by hole filling with area threshold 64, i.e. every
 step of the hot path once. Metric: Gpixel/s over the whole job.
 
 Other workloads: rings8192 (one 8192 x 8192 structured image + fill 64),
-uneven256 (256 images of uneven sizes, batched). The default line also
+uneven256 (256 images of uneven sizes, batched), serve (continuous batching
+of a Poisson frame stream, p50/p99 latency), paper2048 (the paper's Section 6
+protocol: 2048 x 2048 images on a density x granularity grid, reported in
+cycles per pixel beside Table 1). The default line also
 carries the batched-vs-plain ratio measured on uneven256.
 
 --impl reference times the CPU oracle (flood fill, one host thread) on the
@@ -497,13 +500,153 @@ def run_serve(args):
     }
 
 
+# Section 6 / Table 1 of the paper, for context only (one Skylake Gold 6126
+# core at 2.60 GHz, 2048 x 2048 random images, cycles per pixel).
+PAPER_CPP = {"machine": "Skylake Gold 6126 @2.60 GHz, one core",
+             "base_fg_bg_labelling_and_adjacency": [2.80, 15.3], "extra_euler": [0.0, 0.66],
+             "extra_hole_filling": [0.0, 0.74], "extra_features": [0.0, 10.3], "extra_relabeling": [0.59, 13.2],
+             "g4_average_fill_and_features_or_relabel": 5.3}
+
+
+def host_cpu_hz():
+    try:
+        with open("/sys/devices/system/cpu/cpu0/cpufreq/cpuinfo_max_freq") as f:
+            return int(f.read().strip()) * 1e3
+    except (OSError, ValueError):
+        return None
+
+
+def run_paper2048(args):
+    """The paper's measurement protocol (Section 6): 2048 x 2048 random
+    images over a density x granularity grid, each cell timed as the cost per
+    pixel and converted to cycles per pixel with the SM clock sampled during
+    the run. Three modes give Table 1's decomposition on this path:
+      base          labels off: runs, union-find, tree, features, counts
+                    (the Euler number follows from the counts);
+      fill          base + unconditional hole filling (Algorithm 3);
+      relabel_fill  fill + both label images (Algorithm 4).
+    Each cell is one batched call over `per` images of that cell; the passes
+    walk the cells in order, so every call reads inputs that are not in L2."""
+    import copy
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2006_09299_gb300 import ccl, inputs
+    dev = torch.device("cuda", 0)
+    side, per = 2048, args.paper_per_cell
+    D, G = inputs.PAPER_DENSITIES, inputs.PAPER_GRANULARITIES
+    cells = [(i_d, i_g) for i_d in range(len(D)) for i_g in range(len(G))]
+    t_gen = time.perf_counter()
+    d_cells = [[(torch.from_numpy(inputs.paper_sweep_image(i_d, i_g, k)).to(dev), side) for k in range(per)]
+               for i_d, i_g in cells]
+    t_gen = time.perf_counter() - t_gen
+    px_cell = per * side * side
+    ctx = ccl.BatchContext(per, px_cell, side)
+    outs_on = ctx.new_outputs([(side, side)] * per, labels=True, fill=True, device=dev)
+    outs_off = []
+    for o in outs_on:
+        c = copy.copy(o)
+        c.fg = c.bg = None
+        outs_off.append(c)
+    fill_all = np.iinfo(np.int64).max
+    stream = torch.cuda.current_stream(dev)
+
+    def call(mode, imgs):
+        ctx.analyze(imgs, outs=outs_on if mode == "relabel_fill" else outs_off)
+        if mode != "base":
+            ctx.fill_holes(fill_all)
+
+    mid = d_cells[cells.index((10, 3))]
+    tuning = pick_tile_rows(args, ctx, lambda: call("relabel_fill", mid), [(side, side)] * per)
+    modes = ("base", "fill", "relabel_fill")
+    for mode in modes:
+        for imgs in d_cells:
+            call(mode, imgs)
+    torch.cuda.synchronize()
+    if max(o.status() for o in outs_on):
+        raise RuntimeError("device status set during warm-up")
+    passes = max(1, args.steps)
+    times = {m: [[0.0] * passes for _ in cells] for m in modes}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in cells]
+    launches0 = ctx.launch_count()
+    with ClockSampler(0) as clk:
+        for p in range(passes):
+            for mode in modes:
+                for c, imgs in enumerate(d_cells):
+                    ev[c][0].record(stream)
+                    call(mode, imgs)
+                    ev[c][1].record(stream)
+                torch.cuda.synchronize()
+                for c in range(len(cells)):
+                    times[mode][c][p] = ev[c][0].elapsed_time(ev[c][1])
+    launches = ctx.launch_count() - launches0
+    clocks = clk.summary()
+    clock_source = "median sampled SM clock during the timed passes"
+    sm_hz = (clocks.get("sm_mhz") or 0) * 1e6
+    if not sm_hz:
+        sm_hz, clock_source = 2070e6, "nominal maximum SM clock (no samples)"
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    table, summary = {}, {}
+    for mode in modes:
+        ms = [statistics.median(times[mode][c]) for c in range(len(cells))]
+        cpp = [m * 1e-3 * sm_hz / px_cell for m in ms]
+        grid = [[round(cpp[i_d * len(G) + i_g], 5) for i_g in range(len(G))] for i_d in range(len(D))]
+        table[mode] = grid
+        summary[mode] = {
+            "gpu_cpp_min": round(min(cpp), 5), "gpu_cpp_max": round(max(cpp), 5),
+            "gpu_cpp_mean": round(statistics.mean(cpp), 5),
+            "sm_cycles_per_pixel_min": round(min(cpp) * n_sm, 3), "sm_cycles_per_pixel_max": round(max(cpp) * n_sm, 3),
+            "gpixel_per_s": round(len(cells) * px_cell / (sum(ms) * 1e-3) / 1e9, 2),
+            "gpixel_per_s_worst_cell": round(px_cell / (max(ms) * 1e-3) / 1e9, 2),
+            "avg_over_g_by_density": [round(statistics.mean(r), 5) for r in grid],
+            "g4_average": round(statistics.mean(r[G.index(4)] for r in grid), 5),
+        }
+
+    def extra(a, b):
+        diff = [tb - ta for ra, rb in zip(table[a], table[b]) for ta, tb in zip(ra, rb)]
+        return [round(min(diff), 5), round(max(diff), 5)]
+
+    oracle = None
+    if not args.no_cpu_baseline:
+        from oracle import reference as orc
+        orc.build()
+        sample = [(0.5, 1), (0.5, 4)]
+        t_or, px_or = 0.0, 0
+        for d, g in sample:
+            img = inputs.paper_sweep_image(D.index(d), G.index(g))
+            t = time.perf_counter()
+            r = orc.analyze(img, w=side)
+            orc.fill(r, fill_all)
+            t_or += time.perf_counter() - t
+            px_or += side * side
+        hz = host_cpu_hz()
+        oracle = {"kind": "oracle", "cores": 1, "ns_per_pixel": round(t_or / px_or * 1e9, 3),
+                  "cpp": round(t_or / px_or * hz, 2) if hz else None, "host_max_hz": hz,
+                  "sample": "d=0.5 at g=1 and g=4, one image each: labels, tree, features + fill, one host thread"}
+    return {
+        "workload": "paper2048", "metric": "cycles per pixel (Section 6 protocol), 2048x2048 density x granularity",
+        "value": summary["relabel_fill"]["gpu_cpp_mean"], "unit": "GPU cycles/pixel (time x SM clock / pixels)",
+        "higher_is_better": False, "n_gpus": 1, "passes": passes, "dtype": "int32", "data": "synthetic",
+        "config": {"images_per_cell": per, "side": side, "densities": list(D), "granularities": list(G),
+                   "cells": len(cells), "connectivity": "8-fg / 4-bg", "fill_area_threshold": "unbounded (Algorithm 3)",
+                   "tile": tuning, "l2": "each call reads inputs not in L2 (cells walked in order, %d MiB of inputs)"
+                   % (len(cells) * px_cell >> 20), "input_gen_s": round(t_gen, 1)},
+        "sm_count": n_sm, "clock_for_cpp_hz": sm_hz, "clock_source": clock_source, "summary": summary,
+        "extra_fill_cpp": extra("base", "fill"), "extra_relabel_cpp": extra("fill", "relabel_fill"),
+        "table_rows_density_cols_granularity": table, "gpu_launches": launches, "clocks": clocks,
+        "oracle_on_host": oracle, "paper_context": PAPER_CPP,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep4096", choices=["sweep4096", "rings8192", "uneven256", "serve"])
+    ap.add_argument("--workload", default="sweep4096", choices=["sweep4096", "rings8192", "uneven256", "serve", "paper2048"])
+    ap.add_argument("--paper-per-cell", type=int, default=4, help="paper2048: images per density x granularity cell")
     ap.add_argument("--serve-rates", default="250,500,1000,1500,2000,2500,3000,4000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-batch", type=int, default=16)
@@ -518,6 +661,11 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()
+
+    if args.workload == "paper2048" and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_paper2048(args)), flush=True)
+        return
 
     if args.workload == "serve" and args.impl == "ours":
         if rank == 0:

@@ -14,6 +14,9 @@ granularity, Section 4; the exact generator is not given):
                               (1-12 rings, outer radius 4-400, thickness 1-3,
                               spacing >= thickness + 2) OR'd in; gives deep
                               inclusion trees.
+  paper_sweep_image(i_d, i_g, k)
+                              2048 x 2048 granular images on the Section 6
+                              grid: d in {0, 0.05, .., 1} x g in {1..16}.
   uneven_batch(seed, n)       n images with sides drawn log-uniform in
                               [64, 2048], density U(0.2, 0.8), granularity
                               U{1..8}, row pitch rounded up to 128 bytes with
@@ -51,6 +54,18 @@ def sweep_seed(i_d, i_g):
 def sweep_image(i_d, i_g, h=4096, w=4096):
     """One image of the density x granularity sweep."""
     return granular(h, w, SWEEP_DENSITIES[i_d], SWEEP_GRANULARITIES[i_g], sweep_seed(i_d, i_g))
+
+
+PAPER_DENSITIES = tuple(round(0.05 * i, 2) for i in range(21))
+PAPER_GRANULARITIES = tuple(range(1, 17))
+
+
+def paper_sweep_image(i_d, i_g, k=0, side=2048):
+    """Image k of cell (density i_d, granularity i_g) of the Section 6 protocol:
+    side x side random images, densities 0..1 in steps of 0.05, granularities
+    1..16 (the paper sweeps the same two parameters on 2048 x 2048 images)."""
+    seed = 30000 + 1000 * k + 32 * i_d + i_g
+    return granular(side, side, PAPER_DENSITIES[i_d], PAPER_GRANULARITIES[i_g], seed)
 
 
 def rings(h=8192, w=8192, seed=3, n_sets=2000, salt=0.05):
