@@ -74,7 +74,8 @@ struct Scratch {
     uint32_t *nodebits;        // [segs*32] 1 at the first pixel of every node
     uint16_t *run_root;        // [pixels] root ordinal of every run, per tile
     uint32_t *rootinfo;        // [pixels] per local root, see k_label.cu
-    int4 *tstat;               // [tiles] {runs, roots, border roots, 0}
+    int4 *tstat;               // [tiles] {runs, roots, border roots, image}
+    int4 *tsrc;                // [tiles] {first image byte (lo, hi), pitch, rows | copy bytes << 8}
     uint16_t *edges;           // [edge cells] border ordinal of each edge cell's root
     unsigned long long *gp;    // [n_img + edge cells] device-wide union-find
     uint32_t *binfo;           // [same] root ordinal | colour << 16
@@ -123,6 +124,52 @@ __device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p));
     return v;
+}
+
+// ------------------------------------- bulk copies into shared memory
+// One thread issues cp.async.bulk copies (global -> shared, 16-byte aligned,
+// sizes a multiple of 16) that complete on a shared-memory mbarrier; the
+// consumers wait on the barrier's phase parity, a bounded number of times.
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Order this thread's earlier generic-proxy accesses of shared memory
+// before its later bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+constexpr int MBAR_WAIT_LIMIT = 1 << 20;
+
+// True once the phase with the given parity has completed; false when the
+// wait gave up after MBAR_WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < MBAR_WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 // Warp-wide exclusive prefix sum; *total receives the sum over the warp.

@@ -122,6 +122,7 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     s.run_root = (uint16_t *)take(px * 2);
     s.rootinfo = (uint32_t *)take(px * 4);
     s.tstat = (int4 *)take(tiles * 16);
+    s.tsrc = (int4 *)take(tiles * 16);
     s.edges = (uint16_t *)take(edges * 2);
     s.gp = (unsigned long long *)take((1 + edges) * 8);
     s.binfo = (uint32_t *)take((1 + edges) * 4);

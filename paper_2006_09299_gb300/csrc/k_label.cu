@@ -23,14 +23,25 @@ namespace ccl {
 
 // rootinfo layout: bits 0-15 local pixel index of the root's first pixel
 // (row * 1024 + column), bit 16 foreground, bit 17 touches a tile edge,
-// bits 18-29 border ordinal of the root within the tile.
-constexpr int RI_FG = 16, RI_BORDER = 17, RI_KB = 18;
+// bits 18-29 border ordinal of the root within the tile, bit 30 the
+// component has a single run in the tile.
+constexpr int RI_FG = 16, RI_BORDER = 17, RI_KB = 18, RI_SINGLE = 30;
 
 __global__ void k_prologue(Batch B) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *B.s.status = 0;
         for (int k = 0; k < 8; ++k) B.s.work[k] = 0;
+    }
+    if (i < B.n_tiles) {
+        // per tile: its image, and where its rows start for the bulk copies
+        const int img = image_of_tile(B, i);
+        const ImgDesc &d = B.desc[img];
+        const TileGeo g = tile_geo(d, i - d.tile0, B.th);
+        const uint64_t src = (uint64_t)(d.img + (int64_t)g.y0 * d.pitch + g.x0);
+        B.s.tstat[i] = make_int4(0, 0, 0, img);
+        B.s.tsrc[i] = make_int4((int)(uint32_t)src, (int)(uint32_t)(src >> 32), d.pitch,
+                                g.th | (((g.tw + 15) & ~15) << 8));
     }
     if (i >= B.n_img) return;
     const ImgDesc &d = B.desc[i];
@@ -68,19 +79,19 @@ __device__ __forceinline__ int run_start_col(const uint32_t (*sE)[WPR], const ui
     return m ? (l << 5) + 31 - __clz(m) : (int)sRS[r][l];
 }
 
-// Union every run of row r with the runs of row r - 1 it touches, for the
-// contacts whose column lies in word l (32 pixels) and in bits [lo, hi) of
-// that word. Masks mark, once per pair of touching runs, the column where
-// the pair is tested:
-//   va / vb  vertical overlaps of the 8- / 4-adjacent colour, at the first
-//            column of the overlap (where one of the two runs starts);
-//   d1 / d2  diagonal-only contacts of the 8-adjacent colour, up-right and
-//            up-left (Algorithm 2 widens the 8-adjacent run's window by one
-//            pixel on each side).
+// Contacts between row r and row r - 1 whose column lies in word l (32
+// pixels), as bit masks over the word's pixels of row r. Each pair of
+// touching runs is marked once:
+//   mv  vertical overlaps of either colour (8-adjacent: at the first column
+//       of the overlap, where one of the two runs starts; 4-adjacent: the
+//       same), the pixel above is the partner;
+//   m1  diagonal-only contacts of the 8-adjacent colour, up-right: the
+//       partner is the pixel above and to the right (Algorithm 2 widens the
+//       8-adjacent run's window by one pixel on each side);
+//   m2  the same, up-left (a pixel can have both diagonal contacts).
 template <int CONN>
-__device__ __forceinline__ void unify_rows(uint32_t *par, const uint32_t (*sC)[WPR],
-                                           const uint32_t (*sE)[WPR], const uint16_t (*sRS)[WPR], int r,
-                                           int l, int tw, uint32_t range, bool *ok) {
+__device__ __forceinline__ void contact_masks(const uint32_t (*sC)[WPR], const uint32_t (*sE)[WPR], int r, int l,
+                                              int tw, uint32_t *mv, uint32_t *m1, uint32_t *m2) {
     const uint32_t vm = valid_mask(tw, l), vml = valid_mask(tw, l - 1), vmr = valid_mask(tw, l + 1);
     const uint32_t cc = sC[r][l], cu = sC[r - 1][l];
     const uint32_t ec = sE[r][l], eu = sE[r - 1][l];
@@ -98,18 +109,25 @@ __device__ __forceinline__ void unify_rows(uint32_t *par, const uint32_t (*sC)[W
     const uint32_t au_next = (au >> 1) | (aur << 31);
     const uint32_t va = ac & au & ((ec & ac) | (eu & au));
     const uint32_t vb = bc & bu & ((ec & bc) | (eu & bu));
-    const uint32_t d1 = ac & ~au & au_next & ~ac_next;   // (r,x)-(r-1,x+1)
-    const uint32_t d2 = ac & ~au & au_prev & ~ac_prev;   // (r,x)-(r-1,x-1)
-    // (a pixel can have both diagonal contacts: d2 gets its own pass)
-    uint32_t m = (va | vb | d1) & range;
+    *mv = va | vb;
+    *m1 = ac & ~au & au_next & ~ac_next;   // (r,x)-(r-1,x+1)
+    *m2 = ac & ~au & au_prev & ~ac_prev;   // (r,x)-(r-1,x-1)
+}
+
+// Union the runs of each contact in bits `range` of word l of boundary r
+// (row r with row r - 1); the union by minimum of Algorithm 2.
+__device__ __forceinline__ void unite_contacts(uint32_t *par, const uint32_t (*sE)[WPR], const uint16_t (*sRS)[WPR],
+                                               int r, int l, uint32_t mv, uint32_t m1, uint32_t m2, uint32_t range,
+                                               bool *ok) {
+    uint32_t m = (mv | m1) & range;   // disjoint sets of pixels
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
         const int x = 32 * l + b;
-        const int xu = ((d1 >> b) & 1u) ? x + 1 : x;
+        const int xu = ((m1 >> b) & 1u) ? x + 1 : x;
         local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, xu), ok);
     }
-    m = d2 & range;
+    m = m2 & range;
     while (m) {
         const int x = 32 * l + __ffs(m) - 1;
         m &= m - 1;
@@ -129,37 +147,82 @@ __device__ __forceinline__ void compress_row(uint32_t *par, const uint32_t (*sE)
     }
 }
 
+// After the root ordinals are known, par[root] holds them: ordinal (bits
+// 0-14), border ordinal (bits 15-26) and this tag (a run index never has it).
+constexpr uint32_t PAR_TAG = 0x80000000u;
+
+// One CTA per tile at a time, one warp per tile row. The image rows of the
+// next tile are fetched by bulk copies into a staging buffer while the CTA
+// works on the current one: the last warp's lane 0 claims tiles from the
+// work counter one tile ahead and issues the copies as soon as the staging
+// buffer has been read.
+//
+// Root ordinals: the roots of components with more than one run come first
+// (in raster order of their first pixel), then the single-run roots; the
+// feature pass keeps on-chip records for the former only.
 template <int CONN, int TH>
-__global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
-    constexpr int LABEL_THREADS = TH * 16;   // two rows per warp
-    constexpr int LABEL_WARPS = TH / 2;
+__global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
+    constexpr int LABEL_THREADS = TH * 32;   // one row per warp
+    constexpr int LABEL_WARPS = TH;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *par = (uint32_t *)smem;                                    // 4 B per tile pixel
     uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(smem + TH * TW * 4);         // colour bits
     uint32_t(*sE)[WPR] = sC + TH;                                        // run starts
     uint32_t(*sR)[WPR] = sE + TH;                                        // local roots
     uint32_t(*sB)[WPR] = sR + TH;                                        // border roots
-    uint16_t(*sRS)[WPR] = (uint16_t(*)[WPR])(sB + TH);                   // run covering bit 0
+    uint32_t(*sMul)[WPR] = sB + TH;                                      // roots of several runs
+    uint32_t(*sMV)[WPR] = sMul + TH;                                     // contact masks per boundary
+    uint32_t(*sM1)[WPR] = sMV + TH;
+    uint32_t(*sM2)[WPR] = sM1 + TH;
+    uint16_t(*sRS)[WPR] = (uint16_t(*)[WPR])(sM2 + TH);                  // run covering bit 0
     uint16_t(*sRunPre)[WPR] = sRS + TH;                                  // prefix within row
-    uint16_t(*sRootPre)[WPR] = sRunPre + TH;
-    uint16_t(*sBPre)[WPR] = sRootPre + TH;
-    __shared__ int sRowTot[3][TH];
-    __shared__ int sTot[3];
-    __shared__ int sTile, sImg, sFg, sOk;
+    uint16_t(*sMPre)[WPR] = sRunPre + TH;                                // multi-run roots
+    uint16_t(*sSPre)[WPR] = sMPre + TH;                                  // single-run roots
+    uint16_t(*sBPre)[WPR] = sSPre + TH;                                  // border roots
+    uint8_t *stage = (uint8_t *)(sBPre + TH);                            // TH image rows
+    __shared__ int sRowTot[4][TH];   // per row: runs, multi-run roots, border roots, single-run roots
+    __shared__ int sTot[4];
+    __shared__ int sNext, sNextImg, sFg, sOk, sAbort;
+    __shared__ __align__(8) uint64_t sBar;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool issuer = threadIdx.x == LABEL_THREADS - 32;
+    // issuer: copy the rows of tile tn into the staging buffer
+    auto stage_tile = [&](int tn) {
+        const int4 rec = B.s.tsrc[tn];
+        const uint8_t *src = (const uint8_t *)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
+        const int rows = rec.w & 0xFF, bytes = rec.w >> 8;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&sBar, (uint32_t)(rows * bytes));
+        for (int r = 0; r < rows; ++r) bulk_g2s(stage + r * TW, src + (int64_t)r * rec.z, (uint32_t)bytes, &sBar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&sBar, 1);
+        sAbort = 0;
+    }
+    __syncthreads();
+    int claim = 0;   // issuer: the tile claimed for the iteration after next
+    if (issuer) {
+        const int t0 = atomicAdd(&B.s.work[0], 1);
+        int i0 = -1;
+        if (t0 < B.n_tiles) {
+            i0 = B.s.tstat[t0].w;
+            stage_tile(t0);
+        }
+        sNext = t0;
+        sNextImg = i0;
+        claim = atomicAdd(&B.s.work[0], 1);
+    }
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) {
-            const int t = atomicAdd(&B.s.work[0], 1);
-            sTile = t;
-            sImg = t < B.n_tiles ? image_of_tile(B, t) : -1;
             sFg = 0;
             sOk = 1;
         }
         __syncthreads();
-        const int t = sTile;
+        const int t = sNext, img = sNextImg;
         if (t >= B.n_tiles) break;
-        const ImgDesc &d = B.desc[sImg];
+        const ImgDesc &d = B.desc[img];
         const TileGeo g = tile_geo(d, t - d.tile0, TH);
         const int tx = g.tx, y0 = g.y0, x0 = g.x0, th = g.th, tw = g.tw;
         const int64_t rowwords = (int64_t)d.TX * WPR;
@@ -168,13 +231,14 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
         const uint32_t vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
         bool ok = true;
 
-        // ---- read the tile, pack bits, find run starts
+        // ---- the staged rows: pack bits, find run starts (warp = row)
+        if (!mbar_wait(&sBar, phase)) atomicOr(&sAbort, 1);
         for (int r = warp; r < TH; r += LABEL_WARPS) {
             uint32_t word = 0;
             if (r < th && vcnt > 0) {
-                const uint8_t *p = d.img + (int64_t)(y0 + r) * d.pitch + x0 + 32 * lane;
-                uint32_t m = nz16(ld_stream16(p));
-                if (vcnt > 16) m |= nz16(ld_stream16(p + 16)) << 16;
+                const uint4 *p = (const uint4 *)(stage + r * TW + 32 * lane);
+                uint32_t m = nz16(p[0]);
+                if (vcnt > 16) m |= nz16(p[1]) << 16;
                 word = m & vm;
             }
             const uint32_t vr = r < th ? vm : 0u;
@@ -202,36 +266,80 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
             }
         }
         __syncthreads();
+        if (sAbort) {
+            // a copy did not complete: wait once more, bounded, for the copy
+            // in flight, report, and stop
+            if (threadIdx.x == 0) {
+                mbar_wait(&sBar, phase);
+                set_status(B, d, ST_ITER);
+            }
+            break;
+        }
+        phase ^= 1u;
+        // the staging buffer is free: fetch the next tile
+        if (issuer) {
+            const int tn = claim;
+            int in = -1;
+            if (tn < B.n_tiles) {
+                in = B.s.tstat[tn].w;
+                stage_tile(tn);
+            }
+            sNext = tn;
+            sNextImg = in;
+            claim = atomicAdd(&B.s.work[0], 1);
+        }
 
-        // ---- unify each row with the row above (Algorithm 2)
-        // Warp w first unifies its own row pair (2w, 2w + 1) and points row
+        // ---- contacts of every row with the row above (Algorithm 2)
+        // The contact masks of each boundary r (rows r - 1, r) are computed
+        // once, one word per lane, for all levels below. Warp w < TH/2 takes
+        // the odd boundary 2w + 1: it unifies that row pair and points row
         // 2w + 1 at the new roots, like one step of the paper's row-by-row
-        // scan. Then blocks of 4, 8, 16 and 32 rows are joined across their
-        // middle row, one level at a time so that every tree stays a few
-        // links deep; each level's contacts are spread over all threads
-        // (a word's 32 columns split into 2, 4, 8 or 16 slices).
-        if (2 * warp + 1 < th) {
-            unify_rows<CONN>(par, sC, sE, sRS, 2 * warp + 1, lane, tw, FULL, &ok);
-            __syncwarp();
-            compress_row(par, sE, 2 * warp + 1, lane, &ok);
+        // scan; the other warps compute the even boundaries. Then blocks of
+        // 4, 8, 16 and 32 rows are joined across their middle row, one level
+        // at a time so that every tree stays a few links deep; each level's
+        // contacts are spread over all threads (a word's 32 columns split
+        // into 2 ... 32 slices).
+        {
+            const bool pair = warp < TH / 2;
+            const int r = pair ? 2 * warp + 1 : 2 * (warp - TH / 2) + 2;
+            if (r < th) {
+                uint32_t mv = 0, m1 = 0, m2 = 0;
+                if (32 * lane < tw) contact_masks<CONN>(sC, sE, r, lane, tw, &mv, &m1, &m2);
+                sMV[r][lane] = mv;
+                sM1[r][lane] = m1;
+                sM2[r][lane] = m2;
+                if (pair) {
+                    unite_contacts(par, sE, sRS, r, lane, mv, m1, m2, FULL, &ok);
+                    __syncwarp();
+                    compress_row(par, sE, r, lane, &ok);
+                }
+            }
         }
 #pragma unroll 1
         for (int bs = 4; bs <= TH; bs *= 2) {
             __syncthreads();
             const int parts = LABEL_THREADS / ((TH / bs) * WPR);   // slices per word
-            const int t = threadIdx.x;
-            const int j = t / (WPR * parts), l = (t / parts) % WPR, q = t % parts;
+            const int tt = threadIdx.x;
+            const int j = tt / (WPR * parts), l = (tt / parts) % WPR, q = tt % parts;
             const int r = bs * j + bs / 2;
             const int span = 32 / parts;
             const uint32_t range = (span == 32 ? FULL : (((1u << span) - 1u) << (q * span)));
-            if (r < th && 32 * l < tw) unify_rows<CONN>(par, sC, sE, sRS, r, l, tw, range, &ok);
+            if (r < th && 32 * l < tw) {
+                const uint32_t mv = sMV[r][l], m1 = sM1[r][l], m2 = sM2[r][l];
+                if ((mv | m1 | m2) & range) unite_contacts(par, sE, sRS, r, l, mv, m1, m2, range, &ok);
+            }
         }
         __syncthreads();
 
-        // ---- closure: every run points at its root (Algorithm 3, in-tile)
+        // ---- closure: every run points at its root (Algorithm 3, in-tile).
+        // A root is its component's raster-first run, so nothing above
+        // touches it: the component has more runs exactly when the root's
+        // run touches the row below, i.e. holds the upper end of one of the
+        // contacts of boundary r + 1.
         for (int r = warp; r < TH; r += LABEL_WARPS) {
-            uint32_t roots = 0;
-            uint32_t m = r < th ? sE[r][lane] : 0u;
+            uint32_t roots = 0, mul = 0;
+            const uint32_t e = r < th ? sE[r][lane] : 0u;
+            uint32_t m = e;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
@@ -240,12 +348,43 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
                 par[swz(idx)] = (uint32_t)root;
                 if (root == idx) roots |= 1u << b;
             }
+            if (roots && r + 1 < th) {
+                // upper ends of the contacts of boundary r + 1, word l
+                auto upper = [&](int l) -> uint32_t {
+                    const uint32_t m1l = l ? sM1[r + 1][l - 1] : 0u, m2r = l < WPR - 1 ? sM2[r + 1][l + 1] : 0u;
+                    return sMV[r + 1][l] | (sM1[r + 1][l] << 1) | (m1l >> 31) | (sM2[r + 1][l] >> 1) | (m2r << 31);
+                };
+                const uint32_t u = upper(lane);
+                uint32_t mr = roots;
+                while (mr) {
+                    const int b = __ffs(mr) - 1;
+                    mr &= mr - 1;
+                    const uint32_t after = e & ~mask_le(b);   // run starts after b in this word
+                    const uint32_t span = (after ? mask_lt(__ffs(after) - 1) : FULL) & ~mask_lt(b);
+                    bool hit = (u & span) != 0u;
+                    if (!hit && !after) {
+                        // a run reaching past the word's end
+                        for (int l2 = lane + 1; l2 < WPR; ++l2) {
+                            const uint32_t e2 = sE[r][l2];
+                            const uint32_t sp = e2 ? mask_lt(__ffs(e2) - 1) : FULL;
+                            if (upper(l2) & sp) {
+                                hit = true;
+                                break;
+                            }
+                            if (e2) break;
+                        }
+                    }
+                    if (hit) mul |= 1u << b;
+                }
+            }
             sR[r][lane] = roots;
+            sMul[r][lane] = mul;
             sB[r][lane] = 0;
         }
         __syncthreads();
 
-        // ---- roots of the edge cells are border roots
+        // ---- roots of the edge cells are border roots (on the top and
+        // bottom rows one cell per run is enough: the one where it starts)
         const int nedge = 2 * tw + 2 * th;
         for (int i = threadIdx.x; i < nedge; i += LABEL_THREADS) {
             int r, c;
@@ -253,6 +392,7 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
             else if (i < 2 * tw) { r = th - 1; c = i - tw; }
             else if (i < 2 * tw + th) { r = i - 2 * tw; c = 0; }
             else { r = i - 2 * tw - th; c = tw - 1; }
+            if (i < 2 * tw && !((sE[r][c >> 5] >> (c & 31)) & 1u)) continue;
             const int root = par[swz(r * TW + run_start_col(sE, sRS, r, c))];
             atomicOr(&sB[root >> 10][(root >> 5) & 31], 1u << (root & 31));
         }
@@ -260,20 +400,24 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
 
         // ---- ordinals of roots and border roots in raster order
         for (int r = warp; r < TH; r += LABEL_WARPS) {
-            int tr, tb;
-            const int pr = warp_excl_sum(__popc(sR[r][lane]), &tr);
+            const uint32_t rm = sR[r][lane], mul = sMul[r][lane];
+            int tm, ts, tb;
+            const int pm = warp_excl_sum(__popc(rm & mul), &tm);
+            const int ps = warp_excl_sum(__popc(rm & ~mul), &ts);
             const int pb = warp_excl_sum(__popc(sB[r][lane]), &tb);
-            sRootPre[r][lane] = (unsigned short)pr;
+            sMPre[r][lane] = (unsigned short)pm;
+            sSPre[r][lane] = (unsigned short)ps;
             sBPre[r][lane] = (unsigned short)pb;
             if (lane == 0) {
-                sRowTot[1][r] = tr;
+                sRowTot[1][r] = tm;
                 sRowTot[2][r] = tb;
+                sRowTot[3][r] = ts;
             }
         }
         __syncthreads();
         if (warp == 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < 4; ++k) {
                 int tot;
                 const int ex = warp_excl_sum(lane < TH ? sRowTot[k][lane] : 0, &tot);
                 if (lane < TH) sRowTot[k][lane] = ex;
@@ -282,48 +426,56 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
         }
         __syncthreads();
 
-        // ---- outputs
-        if (threadIdx.x == 0) B.s.tstat[t] = make_int4(sTot[0], sTot[1], sTot[2], 0);
+        // ---- per root: record, border slot, ordinal into par[root]
+        if (threadIdx.x == 0) B.s.tstat[t] = make_int4(sTot[0], (int)((uint32_t)sTot[1] | ((uint32_t)sTot[3] << 16)), sTot[2], img);
         uint16_t *rr = B.s.run_root + g.px;
         uint32_t *ri = B.s.rootinfo + g.px;
         const uint32_t slot0 = (uint32_t)(B.n_img + g.b);
+        const int n_multi = sTot[1];
         int nfg = 0;
         for (int r = warp; r < th; r += LABEL_WARPS) {
-            const uint32_t e = sE[r][lane], rm = sR[r][lane], bm = sB[r][lane], c = sC[r][lane];
-            int q = sRowTot[0][r] + sRunPre[r][lane];
-            uint32_t m = e;
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const int root = par[swz(r * TW + 32 * lane + b)];
-                const int rrow = root >> 10, rl = (root >> 5) & 31;
-                const int k = sRowTot[1][rrow] + sRootPre[rrow][rl] +
-                              __popc(sR[rrow][rl] & mask_lt(root & 31));
-                rr[q++] = (uint16_t)k;
-            }
-            int k = sRowTot[1][r] + sRootPre[r][lane];
+            const uint32_t rm = sR[r][lane], bm = sB[r][lane], c = sC[r][lane], mul = sMul[r][lane];
+            int km = sRowTot[1][r] + sMPre[r][lane];
+            int ks = n_multi + sRowTot[3][r] + sSPre[r][lane];
             int kb = sRowTot[2][r] + sBPre[r][lane];
-            m = rm;
+            uint32_t m = rm;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
                 const int idx = r * TW + 32 * lane + b;
-                const uint32_t isb = (bm >> b) & 1u, fg = (c >> b) & 1u;
-                ri[k] = (uint32_t)idx | (fg << RI_FG) | (isb << RI_BORDER) | (isb ? ((uint32_t)kb << RI_KB) : 0u);
+                const uint32_t isb = (bm >> b) & 1u, fg = (c >> b) & 1u, single = ((mul >> b) & 1u) ^ 1u;
+                const int k = single ? ks++ : km++;
+                ri[k] = (uint32_t)idx | (fg << RI_FG) | (isb << RI_BORDER) | (isb ? ((uint32_t)kb << RI_KB) : 0u) |
+                        (single << RI_SINGLE);
+                uint32_t v = PAR_TAG | (uint32_t)k;
                 if (isb) {
                     const uint32_t slot = slot0 + kb;
                     const int64_t key = (int64_t)(y0 + r) * d.w + x0 + 32 * lane + b;
                     B.s.gp[slot] = ((unsigned long long)(key + 1) << 32) | slot;
                     B.s.binfo[slot] = (uint32_t)k | (fg << 16);
+                    v |= (uint32_t)kb << 15;
                     ++kb;
                 } else {
                     nfg += (int)fg;
                 }
-                ++k;
+                par[swz(idx)] = v;
             }
             B.s.nodebits[plane0 + r * rowwords + lane] = rm & ~bm;
         }
-        // edge cells -> border ordinal of their root
+        __syncthreads();
+
+        // ---- per run: root ordinal; per edge cell: border ordinal of its root
+        for (int r = warp; r < th; r += LABEL_WARPS) {
+            int q = sRowTot[0][r] + sRunPre[r][lane];
+            uint32_t m = sE[r][lane];
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                uint32_t v = par[swz(r * TW + 32 * lane + b)];
+                if (!(v & PAR_TAG)) v = par[swz((int)v)];
+                rr[q++] = (uint16_t)(v & 0x7FFFu);
+            }
+        }
         // (cell i of the loop is also its offset: top, bottom, left, right)
         uint16_t *eg = B.s.edges + g.b;
         for (int i = threadIdx.x; i < nedge; i += LABEL_THREADS) {
@@ -332,17 +484,16 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
             else if (i < 2 * tw) { r = th - 1; c = i - tw; }
             else if (i < 2 * tw + th) { r = i - 2 * tw; c = 0; }
             else { r = i - 2 * tw - th; c = tw - 1; }
-            const int off = i;
-            const int root = par[swz(r * TW + run_start_col(sE, sRS, r, c))];
-            const int rrow = root >> 10, rl = (root >> 5) & 31;
-            eg[off] = (uint16_t)(sRowTot[2][rrow] + sBPre[rrow][rl] + __popc(sB[rrow][rl] & mask_lt(root & 31)));
+            uint32_t v = par[swz(r * TW + run_start_col(sE, sRS, r, c))];
+            if (!(v & PAR_TAG)) v = par[swz((int)v)];
+            eg[i] = (uint16_t)((v >> 15) & 0xFFFu);
         }
         nfg = warp_sum(nfg);
         if (lane == 0 && nfg) atomicAdd(&sFg, nfg);
         if (!ok) atomicAnd(&sOk, 0);
         __syncthreads();
         if (threadIdx.x == 0) {
-            if (sFg) atomicAdd(&B.s.img_cnt[4 * sImg + 1], sFg);
+            if (sFg) atomicAdd(&B.s.img_cnt[4 * img + 1], sFg);
             if (!sOk) set_status(B, d, ST_ITER);
         }
         __syncthreads();
@@ -350,33 +501,41 @@ __global__ void __launch_bounds__(TH * 16, TH == 32 ? 1 : 2) k_label(Batch B) {
 }
 
 template <int TH>
-constexpr size_t label_smem() { return (size_t)TH * TW * 4 + 4 * TH * WPR * 4 + 4 * TH * WPR * 2; }
+constexpr size_t label_smem() { return (size_t)TH * TW * 4 + 8 * TH * WPR * 4 + 5 * TH * WPR * 2 + (size_t)TH * TW; }
 
 void launch_prologue(const Batch &B, cudaStream_t st) {
-    k_prologue<<<(B.n_img + 127) / 128, 128, 0, st>>>(B);
+    const int n = B.n_img > B.n_tiles ? B.n_img : B.n_tiles;
+    k_prologue<<<(n + 255) / 256, 256, 0, st>>>(B);
 }
 
 void launch_label(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     if (B.th == 32) {
         const int grid = min(B.n_tiles, c.sms);
         if (B.conn == 0)
-            k_label<0, 32><<<grid, 512, label_smem<32>(), st>>>(B);
+            k_label<0, 32><<<grid, 1024, label_smem<32>(), st>>>(B);
         else
-            k_label<1, 32><<<grid, 512, label_smem<32>(), st>>>(B);
+            k_label<1, 32><<<grid, 1024, label_smem<32>(), st>>>(B);
     } else {
         const int grid = min(B.n_tiles, 2 * c.sms);
         if (B.conn == 0)
-            k_label<0, 16><<<grid, 256, label_smem<16>(), st>>>(B);
+            k_label<0, 16><<<grid, 512, label_smem<16>(), st>>>(B);
         else
-            k_label<1, 16><<<grid, 256, label_smem<16>(), st>>>(B);
+            k_label<1, 16><<<grid, 512, label_smem<16>(), st>>>(B);
     }
 }
 
+template <typename K>
+static cudaError_t configure_smem(K kernel, size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
 cudaError_t configure_label() {
-    cudaError_t e = cudaFuncSetAttribute(k_label<0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<32>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_label<1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<32>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_label<0, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<16>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_label<1, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)label_smem<16>());
+    cudaError_t e = configure_smem(k_label<0, 32>, label_smem<32>());
+    if (e == cudaSuccess) e = configure_smem(k_label<1, 32>, label_smem<32>());
+    if (e == cudaSuccess) e = configure_smem(k_label<0, 16>, label_smem<16>());
+    if (e == cudaSuccess) e = configure_smem(k_label<1, 16>, label_smem<16>());
     return e;
 }
 

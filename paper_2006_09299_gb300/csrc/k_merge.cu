@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(&B.s.work[1], 1);
             sTile = t;
-            sImg = t < B.n_tiles ? image_of_tile(B, t) : -1;
+            sImg = t < B.n_tiles ? B.s.tstat[t].w : -1;
             sFg = 0;
         }
         __syncthreads();
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
         if (threadIdx.x == 0) {
             const int t = atomicAdd(&B.s.work[2], 1);
             sTile = t;
-            sImg = t < B.n_tiles ? image_of_tile(B, t) : -1;
+            sImg = t < B.n_tiles ? B.s.tstat[t].w : -1;
         }
         __syncthreads();
         const int t = sTile;

@@ -19,22 +19,25 @@
 namespace ccl {
 
 
-// Local roots with on-chip feature records (more spill to global atomics).
-template <int TH>
-__host__ __device__ constexpr int maxr() { return TH == 32 ? 4096 : 2048; }
+// Root ordinals of a tile put the roots of components with several runs
+// first, then the single-run roots. Multi-run roots below MAXR accumulate
+// their features in on-chip records (more spill to global atomics); a
+// single-run root's features are those of its run, written when the run is
+// seen. Node ids of the first MAXID roots are kept on chip.
+constexpr int MAXR = 2048;
+constexpr int MAXID = 3584;
 
-// Per local root: S, Sx, Sy, xmin, xmax, row mask (6 words, all updated
-// with native shared reductions) and the node id.
+// Per record: S, Sx, Sy, xmin, xmax, row mask (6 words, all updated with
+// native shared reductions).
 constexpr int REC_WORDS = 6;
 
-// Threads per CTA: 32-row tiles run one 512-thread CTA per SM, 16-row
-// tiles two 256-thread CTAs (16 warps per SM either way).
-template <int TH>
-__host__ __device__ constexpr int write_threads() { return TH == 32 ? 512 : 256; }
+// Two 256-thread CTAs per SM (16 warps): while one waits on its tile's
+// global reads the other streams label rows.
+constexpr int WRITE_THREADS = 256;
 
 template <int TH>
 constexpr size_t write_smem() {
-    return (size_t)maxr<TH>() * (REC_WORDS * 4 + 4) + (size_t)(write_threads<TH>() / 32) * TW * 4 +
+    return (size_t)MAXR * REC_WORDS * 4 + (size_t)MAXID * 4 + MAXID / 8 + (size_t)(WRITE_THREADS / 32) * TW * 4 +
            3 * TH * WPR * 4 + 2 * TH * WPR * 2;
 }
 
@@ -85,9 +88,8 @@ __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e)
 }
 
 template <int TH>
-__global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write(Batch B) {
-    constexpr int MAXR = maxr<TH>();
-    constexpr int NTHREADS = write_threads<TH>();
+__global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
+    constexpr int NTHREADS = WRITE_THREADS;
     constexpr int NWARPS = NTHREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     // feature records of the local roots, structure of arrays (tile-local x, y)
@@ -98,7 +100,8 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
     uint32_t *sX1 = sX0 + MAXR;
     uint32_t *sRows = sX1 + MAXR;                                 // bit r: a run on row r
     int32_t *sId = (int32_t *)(sRows + MAXR);                     // node id per local root
-    int32_t *sRid = sId + MAXR;                                   // per warp: node id per run of a row
+    uint32_t *sBrd = (uint32_t *)(sId + MAXID);                   // bit k: root k touches a tile edge
+    int32_t *sRid = (int32_t *)(sBrd + MAXID / 32);               // per warp: node id per run of a row
     uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(sRid + NWARPS * TW);
     uint32_t(*sE)[WPR] = sC + TH;
     uint32_t(*sNB)[WPR] = sE + TH;
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
         if (threadIdx.x == 0) {
             const int t = atomicAdd(&B.s.work[3], 1);
             sTile = t;
-            sImg = t < B.n_tiles ? image_of_tile(B, t) : -1;
+            sImg = t < B.n_tiles ? B.s.tstat[t].w : -1;
             sOk = 1;
             sCap = 0;
         }
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
         const int64_t cap = d.cap;
         const int n_img = B.n_img;
         const int4 st = B.s.tstat[t];
-        const int n_roots = st.y;
+        const int n_multi = st.y & 0xFFFF, n_roots = n_multi + (int)((uint32_t)st.y >> 16);
         const uint16_t *rr = B.s.run_root + g.px;
         const uint32_t *ri = B.s.rootinfo + g.px;
         const uint32_t slot0 = (uint32_t)(n_img + g.b);
@@ -176,23 +179,33 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
                 const int r = idx >> 10, c = idx & 1023, l = c >> 5;
                 return 1 + sRowSeg[r] + sNBPre[r][l] + __popc(sNB[r][l] & mask_lt(c & 31));
             }
-            const uint32_t root = (uint32_t)B.s.gp[slot0 + (info >> 18)];
+            const uint32_t root = (uint32_t)B.s.gp[slot0 + ((info >> 18) & 0xFFFu)];
             return root < (uint32_t)n_img ? 0 : B.s.canon[root];
         };
 
-        // ---- node ids and feature records of the local roots
-        for (int k = threadIdx.x; k < n_roots; k += NTHREADS) {
-            const uint32_t info = ri[k];
-            const int id = root_id(info);
-            if (k < MAXR) {
-                sId[k] = id;
+        // ---- node ids, edge flags and feature records of the local roots
+        for (int k0 = warp * 32; k0 < n_roots; k0 += NTHREADS) {
+            const int k = k0 + lane;
+            const bool valid = k < n_roots;
+            const uint32_t info = valid ? ri[k] : 0u;
+            const bool isb = (info >> 17) & 1u;
+            const bool multi = k < n_multi;
+            const bool spill = valid && multi && k >= MAXR && !isb;
+            int id = 0;
+            if (valid && (k < MAXID || spill)) id = root_id(info);
+            if (k0 < MAXID) {
+                const uint32_t bal = __ballot_sync(FULL, valid && isb);
+                if (lane == 0) sBrd[k0 >> 5] = bal;
+                if (valid) sId[k] = id;
+            }
+            if (valid && multi && k < MAXR) {
                 sArea[k] = 0u;
                 sSx[k] = 0u;
                 sSy[k] = 0u;
                 sX0[k] = 0xFFFFu;
                 sX1[k] = 0u;
                 sRows[k] = 0u;
-            } else if (!((info >> 17) & 1u) && id < cap) {
+            } else if (spill && id < cap) {
                 d.feat[0 * cap + id] = 0;
                 d.feat[1 * cap + id] = INT64_MAX;
                 d.feat[2 * cap + id] = y0 + ((info & 0xFFFF) >> 10);
@@ -247,7 +260,9 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
                 uint32_t m = e;
                 RunAcc acc0, acc1;
                 auto flush = [&](const RunAcc &a) {
-                    if (a.k < 0) return;
+                    // single-run roots (k >= n_multi) need no accumulation:
+                    // the feature pass reads their run from the bit planes
+                    if (a.k < 0 || a.k >= n_multi) return;
                     if (a.k < MAXR) {
                         atomicAdd(&sArea[a.k], a.len);      // results unused: reductions,
                         atomicAdd(&sSx[a.k], a.sx);         // the lane does not wait
@@ -267,7 +282,7 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
                     m &= m - 1;
                     const int xe = m ? 32 * lane + __ffs(m) - 1 : nxt;
                     const int k = rid[swz(q)];
-                    rid[swz(q)] = k < MAXR ? sId[k] : root_id(ri[k]);
+                    rid[swz(q)] = k < MAXID ? sId[k] : root_id(ri[k]);
                     RunAcc &acc = (q & 1) ? acc1 : acc0;
                     if (k == acc.k) {
                         acc.add(xs, xe);
@@ -380,20 +395,39 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
         }
         __syncthreads();
 
-        // ---- per local root: features
+        // ---- per local root: features (records of multi-run roots; the
+        // run itself for a single-run root)
         hash_init(H);
         __syncthreads();
-        for (int k = threadIdx.x; k < min(n_roots, MAXR); k += NTHREADS) {
+        for (int k = threadIdx.x; k < n_roots; k += NTHREADS) {
+            if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
             const uint32_t info = ri[k];
-            const int r = (info & 0xFFFF) >> 10;
+            const int idx = info & 0xFFFF, r = idx >> 10, c = idx & 1023;
             const bool isb = (info >> 17) & 1u;
-            const int id = sId[k];
+            const int id = k < MAXID ? sId[k] : root_id(info);
             if (id >= cap) continue;
-            const long long area = (long long)sArea[k];
-            const long long sx = (long long)sSx[k] + area * x0;
-            const long long sy = (long long)sSy[k] + area * y0;
-            const int xmin = x0 + (int)sX0[k], xmax = x0 + (int)sX1[k];
-            const int ymax = y0 + 31 - __clz(sRows[k]), ymin = y0 + r;
+            long long area, sx, sy;
+            int xmin, xmax, ymin = y0 + r, ymax;
+            if (k < n_multi) {
+                area = (long long)sArea[k];
+                sx = (long long)sSx[k] + area * x0;
+                sy = (long long)sSy[k] + area * y0;
+                xmin = x0 + (int)sX0[k];
+                xmax = x0 + (int)sX1[k];
+                ymax = y0 + 31 - __clz(sRows[k]);
+            } else {
+                // the run starting at (r, c) ends before the next run start
+                int l = c >> 5;
+                uint32_t m = sE[r][l] & ~mask_le(c & 31);
+                while (!m && ++l < WPR) m = sE[r][l];
+                const int ce = m ? min(32 * l + __ffs(m) - 1, tw) : tw;
+                area = ce - c;
+                sx = (long long)(x0 + c + x0 + ce - 1) * area / 2;
+                sy = (long long)ymin * area;
+                xmin = x0 + c;
+                xmax = x0 + ce - 1;
+                ymax = ymin;
+            }
             if (!isb) {
                 d.feat[0 * cap + id] = area;
                 d.feat[1 * cap + id] = xmin;
@@ -422,15 +456,17 @@ __global__ void __launch_bounds__(write_threads<TH>(), TH == 32 ? 1 : 2) k_write
 
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     if (B.th == 32)
-        k_write<32><<<min(B.n_tiles, c.sms), write_threads<32>(), write_smem<32>(), st>>>(B);
+        k_write<32><<<min(B.n_tiles, 2 * c.sms), WRITE_THREADS, write_smem<32>(), st>>>(B);
     else
-        k_write<16><<<min(B.n_tiles, 2 * c.sms), write_threads<16>(), write_smem<16>(), st>>>(B);
+        k_write<16><<<min(B.n_tiles, 2 * c.sms), WRITE_THREADS, write_smem<16>(), st>>>(B);
 }
 
 cudaError_t configure_write() {
     cudaError_t e = cudaFuncSetAttribute(k_write<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)write_smem<32>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_write<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_write<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)write_smem<16>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_write<16>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 
