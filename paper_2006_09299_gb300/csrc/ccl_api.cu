@@ -139,6 +139,7 @@ static size_t carve(const Limits &L, Scratch *s, ImgDesc **desc, char *base) {
     s->rootinfo = (uint32_t *)take(L.pixels * 4);
     s->tstat = (int4 *)take(L.tiles * 16);
     s->tsrc = (int4 *)take(L.tiles * 16);
+    s->thdr = (TileHdr *)take(L.tiles * sizeof(TileHdr));
     s->edges = (uint16_t *)take(L.edges * 2);
     s->gp = (unsigned long long *)take((L.images + L.edges) * 8);
     s->binfo = (uint32_t *)take((L.images + L.edges) * 4);

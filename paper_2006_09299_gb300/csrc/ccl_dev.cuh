@@ -69,6 +69,16 @@ struct ImgDesc {
 };
 
 // Device scratch, carved out of one allocation by the host.
+// Geometry of one tile, written once per analysis by the prologue and
+// fetched by the tile kernels with a bulk copy ahead of use.
+struct __align__(16) TileHdr {
+    int64_t px;                // first entry of the per-pixel tables
+    int64_t b;                 // first edge cell
+    int64_t b_above;           // first edge cell of the tile above (same column)
+    int64_t seg0;              // the image's first segment
+    int32_t img, tx, y0, x0, th, tw, TX, w;
+};
+
 struct Scratch {
     uint32_t *fgbits;          // [segs*32] foreground bit plane, rows of TX*32 words
     uint32_t *nodebits;        // [segs*32] 1 at the first pixel of every node
@@ -76,6 +86,7 @@ struct Scratch {
     uint32_t *rootinfo;        // [pixels] per local root, see k_label.cu
     int4 *tstat;               // [tiles] {runs, roots, border roots, image}
     int4 *tsrc;                // [tiles] {first image byte (lo, hi), pitch, rows | copy bytes << 8}
+    TileHdr *thdr;             // [tiles]
     uint16_t *edges;           // [edge cells] border ordinal of each edge cell's root
     unsigned long long *gp;    // [n_img + edge cells] device-wide union-find
     uint32_t *binfo;           // [same] root ordinal | colour << 16

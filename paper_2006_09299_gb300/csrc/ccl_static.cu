@@ -123,6 +123,7 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     s.rootinfo = (uint32_t *)take(px * 4);
     s.tstat = (int4 *)take(tiles * 16);
     s.tsrc = (int4 *)take(tiles * 16);
+    s.thdr = (TileHdr *)take(tiles * sizeof(TileHdr));
     s.edges = (uint16_t *)take(edges * 2);
     s.gp = (unsigned long long *)take((1 + edges) * 8);
     s.binfo = (uint32_t *)take((1 + edges) * 4);

@@ -42,6 +42,20 @@ __global__ void k_prologue(Batch B) {
         B.s.tstat[i] = make_int4(0, 0, 0, img);
         B.s.tsrc[i] = make_int4((int)(uint32_t)src, (int)(uint32_t)(src >> 32), d.pitch,
                                 g.th | (((g.tw + 15) & ~15) << 8));
+        TileHdr h;
+        h.px = g.px;
+        h.b = g.b;
+        h.b_above = g.ty > 0 ? tile_geo(d, i - d.tile0 - d.TX, B.th).b : 0;
+        h.seg0 = d.seg0;
+        h.img = img;
+        h.tx = g.tx;
+        h.y0 = g.y0;
+        h.x0 = g.x0;
+        h.th = g.th;
+        h.tw = g.tw;
+        h.TX = d.TX;
+        h.w = d.w;
+        B.s.thdr[i] = h;
     }
     if (i >= B.n_img) return;
     const ImgDesc &d = B.desc[i];
@@ -182,18 +196,21 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
     uint8_t *stage = (uint8_t *)(sBPre + TH);                            // TH image rows
     __shared__ int sRowTot[4][TH];   // per row: runs, multi-run roots, border roots, single-run roots
     __shared__ int sTot[4];
-    __shared__ int sNext, sNextImg, sFg, sOk, sAbort;
+    __shared__ int sNext, sFg, sOk, sAbort;
     __shared__ __align__(8) uint64_t sBar;
+    __shared__ TileHdr sHdr[2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool issuer = threadIdx.x == LABEL_THREADS - 32;
-    // issuer: copy the rows of tile tn into the staging buffer
-    auto stage_tile = [&](int tn) {
+    // issuer: copy the rows and the header of tile tn into the staging
+    // buffer and header slot `slot`
+    auto stage_tile = [&](int tn, int slot) {
         const int4 rec = B.s.tsrc[tn];
         const uint8_t *src = (const uint8_t *)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
         const int rows = rec.w & 0xFF, bytes = rec.w >> 8;
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&sBar, (uint32_t)(rows * bytes));
+        mbar_arrive_expect_tx(&sBar, (uint32_t)(rows * bytes + sizeof(TileHdr)));
+        bulk_g2s(&sHdr[slot], B.s.thdr + tn, (uint32_t)sizeof(TileHdr), &sBar);
         for (int r = 0; r < rows; ++r) bulk_g2s(stage + r * TW, src + (int64_t)r * rec.z, (uint32_t)bytes, &sBar);
     };
     if (threadIdx.x == 0) {
@@ -204,13 +221,8 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
     int claim = 0;   // issuer: the tile claimed for the iteration after next
     if (issuer) {
         const int t0 = atomicAdd(&B.s.work[0], 1);
-        int i0 = -1;
-        if (t0 < B.n_tiles) {
-            i0 = B.s.tstat[t0].w;
-            stage_tile(t0);
-        }
+        if (t0 < B.n_tiles) stage_tile(t0, 0);
         sNext = t0;
-        sNextImg = i0;
         claim = atomicAdd(&B.s.work[0], 1);
     }
     uint32_t phase = 0;
@@ -220,19 +232,21 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             sOk = 1;
         }
         __syncthreads();
-        const int t = sNext, img = sNextImg;
+        const int t = sNext;
         if (t >= B.n_tiles) break;
+        const bool staged = mbar_wait(&sBar, phase);
+        if (!staged) atomicOr(&sAbort, 1);
+        const TileHdr &h = sHdr[phase];
+        const int img = h.img, tx = h.tx, y0 = h.y0, x0 = h.x0;
+        const int th = staged ? h.th : 0, tw = staged ? h.tw : 0;   // nothing is touched on a failed copy
         const ImgDesc &d = B.desc[img];
-        const TileGeo g = tile_geo(d, t - d.tile0, TH);
-        const int tx = g.tx, y0 = g.y0, x0 = g.x0, th = g.th, tw = g.tw;
-        const int64_t rowwords = (int64_t)d.TX * WPR;
-        const int64_t plane0 = (d.seg0 + (int64_t)y0 * d.TX + tx) * WPR;  // word (y0, tile col)
+        const int64_t rowwords = (int64_t)h.TX * WPR;
+        const int64_t plane0 = (h.seg0 + (int64_t)y0 * h.TX + tx) * WPR;  // word (y0, tile col)
         const int vcnt = min(max(tw - 32 * lane, 0), 32);
         const uint32_t vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
         bool ok = true;
 
         // ---- the staged rows: pack bits, find run starts (warp = row)
-        if (!mbar_wait(&sBar, phase)) atomicOr(&sAbort, 1);
         for (int r = warp; r < TH; r += LABEL_WARPS) {
             uint32_t word = 0;
             if (r < th && vcnt > 0) {
@@ -271,21 +285,17 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             // in flight, report, and stop
             if (threadIdx.x == 0) {
                 mbar_wait(&sBar, phase);
-                set_status(B, d, ST_ITER);
+                atomicOr(B.s.status, ST_ITER);
             }
             break;
         }
         phase ^= 1u;
-        // the staging buffer is free: fetch the next tile
+        // the staging buffer and the other header slot are free: fetch the
+        // next tile
         if (issuer) {
             const int tn = claim;
-            int in = -1;
-            if (tn < B.n_tiles) {
-                in = B.s.tstat[tn].w;
-                stage_tile(tn);
-            }
+            if (tn < B.n_tiles) stage_tile(tn, (int)phase);
             sNext = tn;
-            sNextImg = in;
             claim = atomicAdd(&B.s.work[0], 1);
         }
 
@@ -428,9 +438,9 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
 
         // ---- per root: record, border slot, ordinal into par[root]
         if (threadIdx.x == 0) B.s.tstat[t] = make_int4(sTot[0], (int)((uint32_t)sTot[1] | ((uint32_t)sTot[3] << 16)), sTot[2], img);
-        uint16_t *rr = B.s.run_root + g.px;
-        uint32_t *ri = B.s.rootinfo + g.px;
-        const uint32_t slot0 = (uint32_t)(B.n_img + g.b);
+        uint16_t *rr = B.s.run_root + h.px;
+        uint32_t *ri = B.s.rootinfo + h.px;
+        const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
         const int n_multi = sTot[1];
         int nfg = 0;
         for (int r = warp; r < th; r += LABEL_WARPS) {
@@ -450,7 +460,7 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
                 uint32_t v = PAR_TAG | (uint32_t)k;
                 if (isb) {
                     const uint32_t slot = slot0 + kb;
-                    const int64_t key = (int64_t)(y0 + r) * d.w + x0 + 32 * lane + b;
+                    const int64_t key = (int64_t)(y0 + r) * h.w + x0 + 32 * lane + b;
                     B.s.gp[slot] = ((unsigned long long)(key + 1) << 32) | slot;
                     B.s.binfo[slot] = (uint32_t)k | (fg << 16);
                     v |= (uint32_t)kb << 15;
@@ -477,7 +487,7 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             }
         }
         // (cell i of the loop is also its offset: top, bottom, left, right)
-        uint16_t *eg = B.s.edges + g.b;
+        uint16_t *eg = B.s.edges + h.b;
         for (int i = threadIdx.x; i < nedge; i += LABEL_THREADS) {
             int r, c;
             if (i < tw) { r = 0; c = i; }

@@ -108,36 +108,73 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
     uint16_t(*sRunPre)[WPR] = (uint16_t(*)[WPR])(sNB + TH);
     uint16_t(*sNBPre)[WPR] = sRunPre + TH;
     __shared__ int sRowRun[TH], sRowSeg[TH];
-    __shared__ int sTile, sImg, sOk, sCap;
+    __shared__ int sT[2], sOk, sCap, sAbort;
+    __shared__ TileHdr sHdr[2];
+    __shared__ int4 sSt[2];
+    __shared__ __align__(8) uint64_t sHBar;
 
     // the hash table reuses the run buffers once the rows are written
     const HashTab H = hash_carve(sRid);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // thread 0: bulk-copy the header and counts of tile tn into slot `slot`
+    // (tiles are claimed one ahead, so the copy lands during the tile before)
+    auto fetch = [&](int tn, int slot) {
+        sT[slot] = tn;
+        if (tn < B.n_tiles) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&sHBar, (uint32_t)(sizeof(TileHdr) + sizeof(int4)));
+            bulk_g2s(&sHdr[slot], B.s.thdr + tn, (uint32_t)sizeof(TileHdr), &sHBar);
+            bulk_g2s(&sSt[slot], B.s.tstat + tn, (uint32_t)sizeof(int4), &sHBar);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&sHBar, 1);
+        sAbort = 0;
+    }
+    __syncthreads();
+    int claim = 0;
+    if (threadIdx.x == 0) {
+        fetch(atomicAdd(&B.s.work[3], 1), 0);
+        claim = atomicAdd(&B.s.work[3], 1);
+    }
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) {
-            const int t = atomicAdd(&B.s.work[3], 1);
-            sTile = t;
-            sImg = t < B.n_tiles ? B.s.tstat[t].w : -1;
             sOk = 1;
             sCap = 0;
         }
         __syncthreads();
-        const int t = sTile;
+        const int t = sT[phase];
         if (t >= B.n_tiles) break;
-        const ImgDesc &d = B.desc[sImg];
-        const int lt = t - d.tile0;
-        const TileGeo g = tile_geo(d, lt, TH);
-        const int tx = g.tx, y0 = g.y0, x0 = g.x0, th = g.th, tw = g.tw;
-        const int64_t rowwords = (int64_t)d.TX * WPR;
-        const int64_t plane0 = (d.seg0 + (int64_t)y0 * d.TX + tx) * WPR;
+        if (!mbar_wait(&sHBar, phase)) atomicOr(&sAbort, 1);
+        __syncthreads();
+        if (sAbort) {
+            // the header copy did not complete: wait once more (bounded) and stop
+            if (threadIdx.x == 0) {
+                mbar_wait(&sHBar, phase);
+                atomicOr(B.s.status, ST_ITER);
+            }
+            break;
+        }
+        const TileHdr &h = sHdr[phase];
+        const int4 st = sSt[phase];
+        phase ^= 1u;
+        if (threadIdx.x == 0) {
+            fetch(claim, (int)phase);
+            claim = atomicAdd(&B.s.work[3], 1);
+        }
+        const int img = h.img;
+        const ImgDesc &d = B.desc[img];
+        const int tx = h.tx, y0 = h.y0, x0 = h.x0, th = h.th, tw = h.tw;
+        const int64_t rowwords = (int64_t)h.TX * WPR;
+        const int64_t plane0 = (h.seg0 + (int64_t)y0 * h.TX + tx) * WPR;
         const int64_t cap = d.cap;
         const int n_img = B.n_img;
-        const int4 st = B.s.tstat[t];
         const int n_multi = st.y & 0xFFFF, n_roots = n_multi + (int)((uint32_t)st.y >> 16);
-        const uint16_t *rr = B.s.run_root + g.px;
-        const uint32_t *ri = B.s.rootinfo + g.px;
-        const uint32_t slot0 = (uint32_t)(n_img + g.b);
+        const uint16_t *rr = B.s.run_root + h.px;
+        const uint32_t *ri = B.s.rootinfo + h.px;
+        const uint32_t slot0 = (uint32_t)(n_img + h.b);
         const int vcnt = min(max(tw - 32 * lane, 0), 32);
         const uint32_t vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
         bool ok = true, over = false;
@@ -162,7 +199,7 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
             int ntot;
             sNBPre[r][lane] = (uint16_t)warp_excl_sum(__popc(nb), &ntot);
             if (lane == 0)
-                sRowSeg[r] = r < th ? B.s.seg_base[d.seg0 + (int64_t)(y0 + r) * d.TX + tx] - B.s.seg_base[d.seg0] : 0;
+                sRowSeg[r] = r < th ? B.s.seg_base[h.seg0 + (int64_t)(y0 + r) * h.TX + tx] - B.s.seg_base[h.seg0] : 0;
         }
         __syncthreads();
         if (warp == 0) {
@@ -321,8 +358,8 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
                 }
             }
             if (labels) {
-                int32_t *fgrow = d.fg + (int64_t)(y0 + r) * d.w + x0;
-                int32_t *bgrow = d.bg + (int64_t)(y0 + r) * d.w + x0;
+                int32_t *fgrow = d.fg + (int64_t)(y0 + r) * h.w + x0;
+                int32_t *bgrow = d.bg + (int64_t)(y0 + r) * h.w + x0;
 #pragma unroll 2
                 for (int k8 = 0; k8 < TW / 128; ++k8) {
                     const int x = 128 * k8 + 4 * lane;
@@ -380,8 +417,8 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
                 const int id = 1 + sRowSeg[0] + sNBPre[0][lane] + __popc(nb & mask_lt(b));
                 int p = 0;
                 if (y0 > 0) {
-                    const TileGeo ga = tile_geo(d, lt - d.TX, TH);
-                    const uint32_t s2 = (uint32_t)(n_img + ga.b) + B.s.edges[ga.b + edge_bottom(ga, c)];
+                    // the bottom edge cell of the tile above, same column
+                    const uint32_t s2 = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
                     const uint32_t root = (uint32_t)B.s.gp[s2];
                     p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
                 }
@@ -439,7 +476,7 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
             } else {
                 const FeatAcc v{(unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
                                 xmin, ymin, xmax, ymax};
-                hash_push(H, d.feat, cap, sImg, id, v);
+                hash_push(H, d.feat, cap, img, id, v);
             }
         }
         if (!ok) atomicAnd(&sOk, 0);
