@@ -69,6 +69,20 @@ struct ImgDesc {
 };
 
 // Device scratch, carved out of one allocation by the host.
+// Layout of a tile's run_root region, row after row. A dense row of a
+// full-width tile (more than RR_ROUND_MIN runs) is stored round by round: the
+// j-th run starting in word l is at row_slot + 32 j + l, and the row takes 32
+// x (the most runs starting in one word) entries, so that a warp writes 32
+// consecutive entries per round. Other rows are stored in raster order (the
+// row takes as many entries as it has runs).
+constexpr int RR_ROUND_MIN = 256;
+
+__device__ __forceinline__ bool rr_rounds(int tw, int runs_in_row) { return tw == TW && runs_in_row > RR_ROUND_MIN; }
+
+__device__ __forceinline__ int rr_slot(bool rounds, int row_slot, int pre_in_row, int lane, int j) {
+    return rounds ? row_slot + 32 * j + lane : row_slot + pre_in_row + j;
+}
+
 // Geometry of one tile, written once per analysis by the prologue and
 // fetched by the tile kernels with a bulk copy ahead of use.
 struct __align__(16) TileHdr {
@@ -82,7 +96,7 @@ struct __align__(16) TileHdr {
 struct Scratch {
     uint32_t *fgbits;          // [segs*32] foreground bit plane, rows of TX*32 words
     uint32_t *nodebits;        // [segs*32] 1 at the first pixel of every node
-    uint16_t *run_root;        // [pixels] root ordinal of every run, per tile
+    uint16_t *run_root;        // [pixels] root ordinal of every run, per tile (layout: rr_slot)
     uint32_t *rootinfo;        // [pixels] per local root, see k_label.cu
     int4 *tstat;               // [tiles] {runs, roots, border roots, image}
     int4 *tsrc;                // [tiles] {first image byte (lo, hi), pitch, rows | copy bytes << 8}
@@ -190,6 +204,20 @@ __device__ __forceinline__ int warp_excl_sum(int v, int *total) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(FULL, x, 31);
+    return x - v;
+}
+
+// The same over unsigned values (packed 16-bit fields whose sums stay
+// below 2^16 each).
+__device__ __forceinline__ uint32_t warp_excl_sum_u32(uint32_t v, uint32_t *total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
         if (lane >= o) x += y;
     }
     *total = __shfl_sync(FULL, x, 31);

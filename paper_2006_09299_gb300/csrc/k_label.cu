@@ -194,8 +194,11 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
     uint16_t(*sSPre)[WPR] = sMPre + TH;                                  // single-run roots
     uint16_t(*sBPre)[WPR] = sSPre + TH;                                  // border roots
     uint8_t *stage = (uint8_t *)(sBPre + TH);                            // TH image rows
-    __shared__ int sRowTot[4][TH];   // per row: runs, multi-run roots, border roots, single-run roots
-    __shared__ int sTot[4];
+    // per row, then prefixes over rows: runs | run-root slots << 16,
+    // multi-run roots | single-run roots << 16, border roots
+    __shared__ uint32_t sRowTot[3][TH];
+    __shared__ uint32_t sTot[3];
+    __shared__ bool sRounds[TH];
     __shared__ int sNext, sFg, sOk, sAbort;
     __shared__ __align__(8) uint64_t sBar;
     __shared__ TileHdr sHdr[2];
@@ -270,7 +273,12 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             int tot;
             const int pre = warp_excl_sum(__popc(e), &tot);
             sRunPre[r][lane] = (unsigned short)pre;
-            if (lane == 0) sRowTot[0][r] = tot;
+            const bool rounds = rr_rounds(tw, tot);
+            const int slots = rounds ? 32 * __shfl_sync(FULL, warp_incl_max(__popc(e)), 31) : tot;
+            if (lane == 0) {
+                sRowTot[0][r] = (uint32_t)tot | ((uint32_t)slots << 16);
+                sRounds[r] = rounds;
+            }
             uint32_t m = e;
             while (m) {
                 const int b = __ffs(m) - 1;
@@ -419,17 +427,16 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             sSPre[r][lane] = (unsigned short)ps;
             sBPre[r][lane] = (unsigned short)pb;
             if (lane == 0) {
-                sRowTot[1][r] = tm;
+                sRowTot[1][r] = (uint32_t)tm | ((uint32_t)ts << 16);
                 sRowTot[2][r] = tb;
-                sRowTot[3][r] = ts;
             }
         }
         __syncthreads();
         if (warp == 0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                int tot;
-                const int ex = warp_excl_sum(lane < TH ? sRowTot[k][lane] : 0, &tot);
+            for (int k = 0; k < 3; ++k) {
+                uint32_t tot;
+                const uint32_t ex = warp_excl_sum_u32(lane < TH ? sRowTot[k][lane] : 0u, &tot);
                 if (lane < TH) sRowTot[k][lane] = ex;
                 if (lane == 0) sTot[k] = tot;
             }
@@ -437,17 +444,17 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
         __syncthreads();
 
         // ---- per root: record, border slot, ordinal into par[root]
-        if (threadIdx.x == 0) B.s.tstat[t] = make_int4(sTot[0], (int)((uint32_t)sTot[1] | ((uint32_t)sTot[3] << 16)), sTot[2], img);
+        if (threadIdx.x == 0) B.s.tstat[t] = make_int4((int)(sTot[0] & 0xFFFFu), (int)sTot[1], (int)sTot[2], img);
         uint16_t *rr = B.s.run_root + h.px;
         uint32_t *ri = B.s.rootinfo + h.px;
         const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
-        const int n_multi = sTot[1];
+        const int n_multi = (int)(sTot[1] & 0xFFFFu);
         int nfg = 0;
         for (int r = warp; r < th; r += LABEL_WARPS) {
             const uint32_t rm = sR[r][lane], bm = sB[r][lane], c = sC[r][lane], mul = sMul[r][lane];
-            int km = sRowTot[1][r] + sMPre[r][lane];
-            int ks = n_multi + sRowTot[3][r] + sSPre[r][lane];
-            int kb = sRowTot[2][r] + sBPre[r][lane];
+            int km = (int)(sRowTot[1][r] & 0xFFFFu) + sMPre[r][lane];
+            int ks = n_multi + (int)(sRowTot[1][r] >> 16) + sSPre[r][lane];
+            int kb = (int)sRowTot[2][r] + sBPre[r][lane];
             uint32_t m = rm;
             while (m) {
                 const int b = __ffs(m) - 1;
@@ -476,14 +483,16 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
 
         // ---- per run: root ordinal; per edge cell: border ordinal of its root
         for (int r = warp; r < th; r += LABEL_WARPS) {
-            int q = sRowTot[0][r] + sRunPre[r][lane];
+            const bool rounds = sRounds[r];
+            const int row_slot = (int)(sRowTot[0][r] >> 16), pre = sRunPre[r][lane];
             uint32_t m = sE[r][lane];
+            int j = 0;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
                 uint32_t v = par[swz(r * TW + 32 * lane + b)];
                 if (!(v & PAR_TAG)) v = par[swz((int)v)];
-                rr[q++] = (uint16_t)(v & 0x7FFFu);
+                rr[rr_slot(rounds, row_slot, pre, lane, j++)] = (uint16_t)(v & 0x7FFFu);
             }
         }
         // (cell i of the loop is also its offset: top, bottom, left, right)

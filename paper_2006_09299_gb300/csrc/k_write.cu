@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
     uint32_t(*sNB)[WPR] = sE + TH;
     uint16_t(*sRunPre)[WPR] = (uint16_t(*)[WPR])(sNB + TH);
     uint16_t(*sNBPre)[WPR] = sRunPre + TH;
-    __shared__ int sRowRun[TH], sRowSeg[TH];
+    __shared__ int sRowN[TH], sRowSeg[TH], sRowSlot[TH];   // runs, first node, first run-root slot
+    __shared__ bool sRounds[TH];
     __shared__ int sT[2], sOk, sCap, sAbort;
     __shared__ TileHdr sHdr[2];
     __shared__ int4 sSt[2];
@@ -195,7 +196,13 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
             sNB[r][lane] = nb;
             int tot;
             sRunPre[r][lane] = (uint16_t)warp_excl_sum(__popc(e), &tot);
-            if (lane == 0) sRowRun[r] = tot;
+            const bool rounds = rr_rounds(tw, tot);
+            const int slots = rounds ? 32 * __shfl_sync(FULL, warp_incl_max(__popc(e)), 31) : tot;
+            if (lane == 0) {
+                sRowN[r] = tot;
+                sRowSlot[r] = slots;
+                sRounds[r] = rounds;
+            }
             int ntot;
             sNBPre[r][lane] = (uint16_t)warp_excl_sum(__popc(nb), &ntot);
             if (lane == 0)
@@ -204,8 +211,8 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
         __syncthreads();
         if (warp == 0) {
             int tot;
-            const int ex = warp_excl_sum(lane < TH ? sRowRun[lane] : 0, &tot);
-            if (lane < TH) sRowRun[lane] = ex;
+            const int es = warp_excl_sum(lane < TH ? sRowSlot[lane] : 0, &tot);
+            if (lane < TH) sRowSlot[lane] = es;
         }
         __syncthreads();
 
@@ -261,25 +268,41 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
         int pf_row = -1;
         for (int r = warp; r < th; r += NWARPS) {
             const uint32_t e = sE[r][lane];
-            const int rowbase = sRowRun[r];
-            const int nr = (r + 1 < TH ? sRowRun[r + 1] : st.x) - rowbase;
+            const int row_slot = sRowSlot[r], nr = sRowN[r];
             int32_t *rid = sRid + warp * TW;
-            // root ordinals of the row's runs: the first PF * 32 were fetched
-            // into registers while the warp worked on its previous row
+            // root ordinals of the row's runs (rid: by run index within the
+            // row); the first PF rounds were fetched into registers while the
+            // warp worked on its previous row
+            if (sRounds[r]) {
+                // round j of lane l holds the j-th run starting in word l
+                const int pre = sRunPre[r][lane], cnt = __popc(e);
 #pragma unroll
-            for (int j = 0; j < PF; ++j) {
-                const int i = lane + 32 * j;
-                if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[rowbase + i];
+                for (int j = 0; j < PF; ++j)
+                    if (j < cnt) rid[swz(pre + j)] = pf_row == r ? pf[j] : (int)rr[row_slot + 32 * j + lane];
+                for (int j = PF; j < cnt; ++j) rid[swz(pre + j)] = rr[row_slot + 32 * j + lane];
+            } else {
+#pragma unroll
+                for (int j = 0; j < PF; ++j) {
+                    const int i = lane + 32 * j;
+                    if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[row_slot + i];
+                }
+                for (int i = lane + 32 * PF; i < nr; i += 32) rid[swz(i)] = rr[row_slot + i];
             }
-            for (int i = lane + 32 * PF; i < nr; i += 32) rid[swz(i)] = rr[rowbase + i];
             {
                 const int rn = r + NWARPS;   // this warp's next row
                 if (rn < th) {
-                    const int nb = sRowRun[rn], nn = (rn + 1 < TH ? sRowRun[rn + 1] : st.x) - nb;
+                    const int ns = sRowSlot[rn];
+                    if (sRounds[rn]) {
+                        const int cn = __popc(sE[rn][lane]);
 #pragma unroll
-                    for (int j = 0; j < PF; ++j) {
-                        const int i = lane + 32 * j;
-                        pf[j] = i < nn ? (int)rr[nb + i] : 0;
+                        for (int j = 0; j < PF; ++j) pf[j] = j < cn ? (int)rr[ns + 32 * j + lane] : 0;
+                    } else {
+                        const int nb = ns, nn = sRowN[rn];
+#pragma unroll
+                        for (int j = 0; j < PF; ++j) {
+                            const int i = lane + 32 * j;
+                            pf[j] = i < nn ? (int)rr[nb + i] : 0;
+                        }
                     }
                     pf_row = rn;
                 }
