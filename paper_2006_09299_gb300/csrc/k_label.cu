@@ -333,15 +333,16 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
                 }
             }
         }
+        constexpr int LG_TH = TH == 32 ? 5 : 4;   // one warp per row: LABEL_THREADS = 32 TH
 #pragma unroll 1
-        for (int bs = 4; bs <= TH; bs *= 2) {
+        for (int lb = 2; lb <= LG_TH; ++lb) {    // blocks of 2^lb rows
             __syncthreads();
-            const int parts = LABEL_THREADS / ((TH / bs) * WPR);   // slices per word
-            const int tt = threadIdx.x;
-            const int j = tt / (WPR * parts), l = (tt / parts) % WPR, q = tt % parts;
-            const int r = bs * j + bs / 2;
-            const int span = 32 / parts;
-            const uint32_t range = (span == 32 ? FULL : (((1u << span) - 1u) << (q * span)));
+            // TH / 2^lb boundaries x 32 words, each word split into 2^lp slices
+            const int lp = lb, tt = threadIdx.x;
+            const int j = tt >> (5 + lp), l = (tt >> lp) & 31, q = tt & ((1 << lp) - 1);
+            const int r = (j << lb) + (1 << (lb - 1));
+            const int span = 32 >> lp;
+            const uint32_t range = (((1u << span) - 1u) << (q * span));
             if (r < th && 32 * l < tw) {
                 const uint32_t mv = sMV[r][l], m1 = sM1[r][l], m2 = sM2[r][l];
                 if ((mv | m1 | m2) & range) unite_contacts(par, sE, sRS, r, l, mv, m1, m2, range, &ok);

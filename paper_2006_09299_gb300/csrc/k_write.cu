@@ -181,12 +181,26 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
         bool ok = true, over = false;
 
         // ---- bit planes of the tile: colour, run starts, node first-pixels
-        for (int r = warp; r < TH; r += NWARPS) {
-            uint32_t c = 0, nb = 0;
+        // (all of this warp's rows are loaded before any is used)
+        constexpr int RPW = TH / NWARPS;   // rows per warp
+        uint32_t cw[RPW], nbw[RPW];
+        int segw[RPW];
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const int r = warp + i * NWARPS;
+            cw[i] = nbw[i] = 0u;
+            segw[i] = 0;
             if (r < th) {
-                c = B.s.fgbits[plane0 + r * rowwords + lane];
-                nb = B.s.nodebits[plane0 + r * rowwords + lane];
+                cw[i] = B.s.fgbits[plane0 + r * rowwords + lane];
+                nbw[i] = B.s.nodebits[plane0 + r * rowwords + lane];
+                if (lane == 0) segw[i] = B.s.seg_base[h.seg0 + (int64_t)(y0 + r) * h.TX + tx];
             }
+        }
+        const int seg_first = lane == 0 ? B.s.seg_base[h.seg0] : 0;
+#pragma unroll
+        for (int i = 0; i < RPW; ++i) {
+            const int r = warp + i * NWARPS;
+            const uint32_t c = cw[i], nb = nbw[i];
             const uint32_t vr = r < th ? vm : 0u;
             const uint32_t left = __shfl_up_sync(FULL, c, 1);
             const uint32_t prev = (c << 1) | (lane ? (left >> 31) : 0u);
@@ -205,8 +219,7 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
             }
             int ntot;
             sNBPre[r][lane] = (uint16_t)warp_excl_sum(__popc(nb), &ntot);
-            if (lane == 0)
-                sRowSeg[r] = r < th ? B.s.seg_base[h.seg0 + (int64_t)(y0 + r) * h.TX + tx] - B.s.seg_base[h.seg0] : 0;
+            if (lane == 0) sRowSeg[r] = r < th ? segw[i] - seg_first : 0;
         }
         __syncthreads();
         if (warp == 0) {
@@ -228,10 +241,12 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
         };
 
         // ---- node ids, edge flags and feature records of the local roots
+        uint32_t info_next = warp * 32 + lane < n_roots ? ri[warp * 32 + lane] : 0u;   // one iteration ahead
         for (int k0 = warp * 32; k0 < n_roots; k0 += NTHREADS) {
             const int k = k0 + lane;
             const bool valid = k < n_roots;
-            const uint32_t info = valid ? ri[k] : 0u;
+            const uint32_t info = info_next;
+            if (k + NTHREADS < n_roots) info_next = ri[k + NTHREADS];
             const bool isb = (info >> 17) & 1u;
             const bool multi = k < n_multi;
             const bool spill = valid && multi && k >= MAXR && !isb;
@@ -459,9 +474,11 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
         // run itself for a single-run root)
         hash_init(H);
         __syncthreads();
+        uint32_t fin_next = threadIdx.x < n_roots ? ri[threadIdx.x] : 0u;   // one iteration ahead
         for (int k = threadIdx.x; k < n_roots; k += NTHREADS) {
+            const uint32_t info = fin_next;
+            if (k + NTHREADS < n_roots) fin_next = ri[k + NTHREADS];
             if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
-            const uint32_t info = ri[k];
             const int idx = info & 0xFFFF, r = idx >> 10, c = idx & 1023;
             const bool isb = (info >> 17) & 1u;
             const int id = k < MAXID ? sId[k] : root_id(info);
