@@ -2,9 +2,11 @@
 //
 // The paper's steps 1a and 1b (Algorithms 1 and 2) scan one row at a time and
 // grow one equivalence table for the whole image. Here every tile of 32 rows
-// x 1024 columns is handled by one CTA, all rows at once:
-//   - the tile is read with 16-byte loads and packed into a 1-bit-per-pixel
-//     plane, one 32-bit word per lane (1024 columns = one warp);
+// x 1024 columns (or 16 rows) is handled by one CTA, all rows at once:
+//   - the tile's rows arrive by bulk copies (cp.async.bulk) into shared
+//     memory, issued while the CTA works on the previous tile, and are packed
+//     into a 1-bit-per-pixel plane, one 32-bit word per lane (1024 columns =
+//     one warp, one warp per row);
 //   - run starts come from an XOR of each word with itself shifted by one
 //     pixel (Algorithm 1's edge detection x0 xor x1), 32 pixels at a time;
 //   - the overlap tests of Algorithm 2 become word masks between a row and
@@ -146,18 +148,6 @@ __device__ __forceinline__ void unite_contacts(uint32_t *par, const uint32_t (*s
         const int x = 32 * l + __ffs(m) - 1;
         m &= m - 1;
         local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, x - 1), ok);
-    }
-}
-
-// Point every run of row r at its current root.
-__device__ __forceinline__ void compress_row(uint32_t *par, const uint32_t (*sE)[WPR], int r, int lane,
-                                             bool *ok) {
-    uint32_t m = sE[r][lane];
-    while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int idx = r * TW + 32 * lane + b;
-        par[swz(idx)] = (uint32_t)local_find(par, idx, ok);
     }
 }
 
@@ -308,45 +298,20 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
         }
 
         // ---- contacts of every row with the row above (Algorithm 2)
-        // The contact masks of each boundary r (rows r - 1, r) are computed
-        // once, one word per lane, for all levels below. Warp w < TH/2 takes
-        // the odd boundary 2w + 1: it unifies that row pair and points row
-        // 2w + 1 at the new roots, like one step of the paper's row-by-row
-        // scan; the other warps compute the even boundaries. Then blocks of
-        // 4, 8, 16 and 32 rows are joined across their middle row, one level
-        // at a time so that every tree stays a few links deep; each level's
-        // contacts are spread over all threads (a word's 32 columns split
-        // into 2 ... 32 slices).
-        {
-            const bool pair = warp < TH / 2;
-            const int r = pair ? 2 * warp + 1 : 2 * (warp - TH / 2) + 2;
-            if (r < th) {
-                uint32_t mv = 0, m1 = 0, m2 = 0;
-                if (32 * lane < tw) contact_masks<CONN>(sC, sE, r, lane, tw, &mv, &m1, &m2);
-                sMV[r][lane] = mv;
-                sM1[r][lane] = m1;
-                sM2[r][lane] = m2;
-                if (pair) {
-                    unite_contacts(par, sE, sRS, r, lane, mv, m1, m2, FULL, &ok);
-                    __syncwarp();
-                    compress_row(par, sE, r, lane, &ok);
-                }
-            }
-        }
-        constexpr int LG_TH = TH == 32 ? 5 : 4;   // one warp per row: LABEL_THREADS = 32 TH
-#pragma unroll 1
-        for (int lb = 2; lb <= LG_TH; ++lb) {    // blocks of 2^lb rows
-            __syncthreads();
-            // TH / 2^lb boundaries x 32 words, each word split into 2^lp slices
-            const int lp = lb, tt = threadIdx.x;
-            const int j = tt >> (5 + lp), l = (tt >> lp) & 31, q = tt & ((1 << lp) - 1);
-            const int r = (j << lb) + (1 << (lb - 1));
-            const int span = 32 >> lp;
-            const uint32_t range = (((1u << span) - 1u) << (q * span));
-            if (r < th && 32 * l < tw) {
-                const uint32_t mv = sMV[r][l], m1 = sM1[r][l], m2 = sM2[r][l];
-                if ((mv | m1 | m2) & range) unite_contacts(par, sE, sRS, r, l, mv, m1, m2, range, &ok);
-            }
+        // Warp r - 1 takes boundary r (rows r - 1 and r), one word per lane:
+        // it computes the boundary's contact masks (kept for the closure
+        // below) and unites the runs of each contact. All boundaries are
+        // united at the same time: the union by minimum with atomicMin stays
+        // correct under concurrent unions, and the paper's row-by-row order
+        // only matters for the provisional labels, not for the classes.
+        if (warp + 1 < th) {
+            const int r = warp + 1;
+            uint32_t mv = 0, m1 = 0, m2 = 0;
+            if (32 * lane < tw) contact_masks<CONN>(sC, sE, r, lane, tw, &mv, &m1, &m2);
+            sMV[r][lane] = mv;
+            sM1[r][lane] = m1;
+            sM2[r][lane] = m2;
+            if (mv | m1 | m2) unite_contacts(par, sE, sRS, r, lane, mv, m1, m2, FULL, &ok);
         }
         __syncthreads();
 
