@@ -232,11 +232,7 @@ def run_ours(args, rank, world, local_rank):
     ms = t0.elapsed_time(t1) / args.steps
     launches = ctx.launch_count() - launches0
     clocks = clk.summary()
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * px / (ms * 1e-3) / 1e9
+    ms, value = replica_throughput(ms, px, world, dev)
 
     # ---- per-kernel device time over a second timed region (phase events)
     ctx.enable_phase_timing(2 * args.steps)
@@ -293,6 +289,19 @@ def run_ours(args, rank, world, local_rank):
     }
     res.update(extra)
     return res
+
+
+def replica_throughput(ms, px, world, device):
+    """Replicas (one process per GPU, the same workload on each, no data
+    exchange): the job time is the slowest rank's, and the job processed
+    world x px pixels. Returns (max-over-ranks ms per step, whole-job
+    Gpixel/s). Works on any process group (nccl on GPUs, gloo in tests)."""
+    if world > 1:
+        import torch
+        tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, world * px / (ms * 1e-3) / 1e9
 
 
 def pick_tile_rows(args, ctx, step, shapes):
