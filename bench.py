@@ -9,7 +9,7 @@ step of the hot path once. Metric: Gpixel/s over the whole job.
 
 Other workloads: rings8192 (one 8192 x 8192 structured image + fill 64),
 uneven256 (256 images of uneven sizes, batched), serve (continuous batching
-of a Poisson frame stream, p50/p99 latency), paper2048 (the paper's Section 6
+of a Poisson frame stream, p50/p99 latency), paper2048 (the paper's Section 4
 protocol: 2048 x 2048 images on a density x granularity grid, reported in
 cycles per pixel beside Table 1). The default line also
 carries the batched-vs-plain ratio measured on uneven256.
@@ -517,7 +517,7 @@ def run_serve(args):
     }
 
 
-# Section 6 / Table 1 of the paper, for context only (one Skylake Gold 6126
+# Section 4 / Table 1 of the paper, for context only (one Skylake Gold 6126
 # core at 2.60 GHz, 2048 x 2048 random images, cycles per pixel).
 PAPER_CPP = {"machine": "Skylake Gold 6126 @2.60 GHz, one core",
              "base_fg_bg_labelling_and_adjacency": [2.80, 15.3], "extra_euler": [0.0, 0.66],
@@ -534,7 +534,7 @@ def host_cpu_hz():
 
 
 def run_paper2048(args):
-    """The paper's measurement protocol (Section 6): 2048 x 2048 random
+    """The paper's measurement protocol (Section 4): 2048 x 2048 random
     images over a density x granularity grid, each cell timed as the cost per
     pixel and converted to cycles per pixel with the SM clock sampled during
     the run. Three modes give Table 1's decomposition on this path:
@@ -642,7 +642,7 @@ def run_paper2048(args):
                   "cpp": round(t_or / px_or * hz, 2) if hz else None, "host_max_hz": hz,
                   "sample": "d=0.5 at g=1 and g=4, one image each: labels, tree, features + fill, one host thread"}
     return {
-        "workload": "paper2048", "metric": "cycles per pixel (Section 6 protocol), 2048x2048 density x granularity",
+        "workload": "paper2048", "metric": "cycles per pixel (Section 4 protocol), 2048x2048 density x granularity",
         "value": summary["relabel_fill"]["gpu_cpp_mean"], "unit": "GPU cycles/pixel (time x SM clock / pixels)",
         "higher_is_better": False, "n_gpus": 1, "passes": passes, "dtype": "int32", "data": "synthetic",
         "config": {"images_per_cell": per, "side": side, "densities": list(D), "granularities": list(G),

@@ -17,7 +17,8 @@
  *     pixels). Bytes at x >= w are never interpreted.
  *   - Foreground components use 8-adjacency and background components
  *     4-adjacency (Algorithm 2); ccl_set_connectivity selects the
- *     complementary pair (Section 3.2, remark on line c8 of Algorithm 2).
+ *     complementary pair (Section 3.2: the 8-adjacency switch of Algorithm 2
+ *     taken for the other colour).
  *   - Node 0 is the exterior: the background component made of every
  *     background pixel connected to the image border (Section 3.1 defines
  *     surrounding through paths to the exterior of the image). It exists even

@@ -15,7 +15,7 @@ granularity, Section 4; the exact generator is not given):
                               spacing >= thickness + 2) OR'd in; gives deep
                               inclusion trees.
   paper_sweep_image(i_d, i_g, k)
-                              2048 x 2048 granular images on the Section 6
+                              2048 x 2048 granular images on the Section 4
                               grid: d in {0, 0.05, .., 1} x g in {1..16}.
   uneven_batch(seed, n)       n images with sides drawn log-uniform in
                               [64, 2048], density U(0.2, 0.8), granularity
@@ -61,7 +61,7 @@ PAPER_GRANULARITIES = tuple(range(1, 17))
 
 
 def paper_sweep_image(i_d, i_g, k=0, side=2048):
-    """Image k of cell (density i_d, granularity i_g) of the Section 6 protocol:
+    """Image k of cell (density i_d, granularity i_g) of the Section 4 protocol:
     side x side random images, densities 0..1 in steps of 0.05, granularities
     1..16 (the paper sweeps the same two parameters on 2048 x 2048 images)."""
     seed = 30000 + 1000 * k + 32 * i_d + i_g
