@@ -27,9 +27,9 @@ namespace ccl {
 constexpr int MAXR = 2048;
 constexpr int MAXID = 3584;
 
-// Per record: S, Sx, Sy, xmin, xmax, row mask (6 words, all updated with
-// native shared reductions).
-constexpr int REC_WORDS = 6;
+// Per record: S, Sx, Sy, xmin, xmax and the row mask, all updated with
+// native 32-bit shared reductions (a packed 64-bit sum was slower).
+constexpr int REC_BYTES = 6 * 4;
 
 // Two 256-thread CTAs per SM (16 warps): while one waits on its tile's
 // global reads the other streams label rows.
@@ -37,7 +37,7 @@ constexpr int WRITE_THREADS = 256;
 
 template <int TH>
 constexpr size_t write_smem() {
-    return (size_t)MAXR * REC_WORDS * 4 + (size_t)MAXID * 4 + MAXID / 8 + (size_t)(WRITE_THREADS / 32) * TW * 4 +
+    return (size_t)MAXR * REC_BYTES + (size_t)MAXID * 4 + MAXID / 8 + (size_t)(WRITE_THREADS / 32) * TW * 4 +
            3 * TH * WPR * 4 + 2 * TH * WPR * 2;
 }
 
@@ -65,6 +65,8 @@ struct RunAcc {
 // of consecutive lanes with the same root keeps it (the others get k = -1).
 __device__ __forceinline__ void warp_combine(RunAcc &a, int lane) {
     const int kprev = __shfl_up_sync(FULL, a.k, 1);
+    // nothing to combine unless two consecutive lanes hold the same root
+    if (!__any_sync(FULL, lane > 0 && a.k >= 0 && kprev == a.k)) return;
     const bool head = lane == 0 || kprev != a.k;
     int seg = head ? lane : 0;               // lane of this group's first member
 #pragma unroll
@@ -294,14 +296,29 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
 #pragma unroll
                 for (int j = 0; j < PF; ++j)
                     if (j < cnt) rid[swz(pre + j)] = pf_row == r ? pf[j] : (int)rr[row_slot + 32 * j + lane];
-                for (int j = PF; j < cnt; ++j) rid[swz(pre + j)] = rr[row_slot + 32 * j + lane];
+                // the rest in groups of 8 loads in flight
+                for (int j0 = PF; j0 < cnt; j0 += 8) {
+                    int v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = j0 + u < cnt ? (int)rr[row_slot + 32 * (j0 + u) + lane] : 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (j0 + u < cnt) rid[swz(pre + j0 + u)] = v[u];
+                }
             } else {
 #pragma unroll
                 for (int j = 0; j < PF; ++j) {
                     const int i = lane + 32 * j;
                     if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[row_slot + i];
                 }
-                for (int i = lane + 32 * PF; i < nr; i += 32) rid[swz(i)] = rr[row_slot + i];
+                for (int i0 = lane + 32 * PF; i0 < nr; i0 += 8 * 32) {
+                    int v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < nr ? (int)rr[row_slot + i0 + 32 * u] : 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (i0 + 32 * u < nr) rid[swz(i0 + 32 * u)] = v[u];
+                }
             }
             {
                 const int rn = r + NWARPS;   // this warp's next row
@@ -339,8 +356,9 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
                     // the feature pass reads their run from the bit planes
                     if (a.k < 0 || a.k >= n_multi) return;
                     if (a.k < MAXR) {
-                        atomicAdd(&sArea[a.k], a.len);      // results unused: reductions,
-                        atomicAdd(&sSx[a.k], a.sx);         // the lane does not wait
+                        // results unused: reductions, the lane does not wait
+                        atomicAdd(&sArea[a.k], a.len);
+                        atomicAdd(&sSx[a.k], a.sx);
                         atomicAdd(&sSy[a.k], (uint32_t)r * a.len);
                         atomicMin(&sX0[a.k], (uint32_t)a.x0);
                         atomicMax(&sX1[a.k], (uint32_t)a.x1);
@@ -352,13 +370,14 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
                                         (unsigned long long)(y0 + r) * a.len, x0 + a.x0, y0 + r, x0 + a.x1, y0 + r);
                     }
                 };
-                while (m) {
+                // one run into the accumulator of its parity (the caller
+                // alternates acc0 / acc1 statically)
+                auto step = [&](RunAcc &acc) {
                     const int xs = 32 * lane + __ffs(m) - 1;
                     m &= m - 1;
                     const int xe = m ? 32 * lane + __ffs(m) - 1 : nxt;
                     const int k = rid[swz(q)];
                     rid[swz(q)] = k < MAXID ? sId[k] : root_id(ri[k]);
-                    RunAcc &acc = (q & 1) ? acc1 : acc0;
                     if (k == acc.k) {
                         acc.add(xs, xe);
                     } else {
@@ -366,6 +385,12 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
                         acc.start(k, xs, xe);
                     }
                     ++q;
+                };
+                if ((q & 1) && m) step(acc1);
+                while (m) {
+                    step(acc0);
+                    if (!m) break;
+                    step(acc1);
                 }
                 // the last accumulators of neighbouring lanes often hold the
                 // same root (a component crossing the row many times): combine
