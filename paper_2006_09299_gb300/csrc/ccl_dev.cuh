@@ -321,10 +321,28 @@ __device__ __forceinline__ int local_find(const uint32_t *par, int a, bool *ok) 
     return a;
 }
 
+// Find with path halving: every other node on the way up is pointed at its
+// grandparent, which is one of its ancestors whatever unions run at the same
+// time (links only ever point at smaller indices of the same class). A later
+// phase that needs every run to point straight at its root must therefore
+// not run concurrently with this one.
+__device__ __forceinline__ int local_find_halving(uint32_t *par, int a, bool *ok) {
+    for (int it = 0; it < LOCAL_FIND_LIMIT; ++it) {
+        const int p = (int)*(volatile uint32_t *)(par + swz(a));
+        if (p == a) return a;
+        const int gp = (int)*(volatile uint32_t *)(par + swz(p));
+        if (gp == p) return p;
+        *(volatile uint32_t *)(par + swz(a)) = (uint32_t)gp;
+        a = gp;
+    }
+    *ok = false;
+    return a;
+}
+
 __device__ __forceinline__ void local_union(uint32_t *par, int a, int b, bool *ok) {
     for (int it = 0; it < LOCAL_UNION_LIMIT; ++it) {
-        a = local_find(par, a, ok);
-        b = local_find(par, b, ok);
+        a = local_find_halving(par, a, ok);
+        b = local_find_halving(par, b, ok);
         if (a == b || !*ok) return;
         if (a < b) { const int t = a; a = b; b = t; }
         const int old = (int)atomicMin(par + swz(a), (uint32_t)b);
