@@ -157,8 +157,17 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
                 }
             }
         }
-        // segmented inclusive scan over lanes with equal keys
+        // segmented inclusive scan over lanes with equal keys (skipped when
+        // no lane has anything to add, or no two neighbours share a survivor)
+        if (!__any_sync(FULL, key >= 0)) continue;
         const long long kprev = __shfl_up_sync(FULL, key, 1);
+        if (!__any_sync(FULL, key >= 0 && lane > 0 && kprev == key)) {
+            if (key >= 0) {
+                const ImgDesc &d = B.desc[img];
+                hash_push(H, d.filled_feat, d.cap, img, (int)(uint32_t)key, v);
+            }
+            continue;
+        }
         int seg = (lane == 0 || kprev != key) ? lane : 0;
 #pragma unroll
         for (int dd = 1; dd < 32; dd <<= 1) seg = max(seg, __shfl_up_sync(FULL, seg, dd));
