@@ -193,43 +193,34 @@ __global__ void k_merge(Batch B) {
     if (!ok) set_status(B, B.desc[img], ST_ITER);
 }
 
-// One CTA per tile: settle the final root of each border root.
+// One warp per tile (tiles strided over all warps of the grid): settle the
+// final root of each border root.
 __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
-    __shared__ int sFg;
-    __shared__ int sTile, sImg;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const int t = atomicAdd(&B.s.work[1], 1);
-            sTile = t;
-            sImg = t < B.n_tiles ? B.s.tstat[t].w : -1;
-            sFg = 0;
-        }
-        __syncthreads();
-        const int t = sTile;
-        if (t >= B.n_tiles) break;
-        const ImgDesc &d = B.desc[sImg];
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (NTHREADS / 32);
+    for (int t = blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5); t < B.n_tiles; t += nwarps) {
+        const TileHdr &h = B.s.thdr[t];
+        const int img = h.img;
+        const ImgDesc &d = B.desc[img];
         const int nb = B.s.tstat[t].z;
-        const uint32_t slot0 = (uint32_t)(B.n_img + tile_geo(d, t - d.tile0, B.th).b);
+        const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
         bool ok = true;
         int nfg = 0;
-        for (int kb = threadIdx.x; kb < nb; kb += NTHREADS) {
+        for (int kb = lane; kb < nb; kb += 32) {
             const uint32_t slot = slot0 + kb;
             const uint32_t root = global_find(B.s.gp, slot, &ok);
             if (root != slot) {
                 B.s.gp[slot] = ld_volatile_u64(B.s.gp + root);
             } else {
                 const int64_t key = (int64_t)(B.s.gp[slot] >> 32) - 1;
-                const int y = (int)(key / d.w), x = (int)(key - (int64_t)y * d.w);
-                atomicOr(&B.s.nodebits[(d.seg0 + (int64_t)y * d.TX) * WPR + (x >> 5)], 1u << (x & 31));
+                const int y = (int)(key / h.w), x = (int)(key - (int64_t)y * h.w);
+                atomicOr(&B.s.nodebits[(h.seg0 + (int64_t)y * h.TX) * WPR + (x >> 5)], 1u << (x & 31));
                 nfg += (B.s.binfo[slot] >> 16) & 1;
             }
         }
         nfg = warp_sum(nfg);
-        if ((threadIdx.x & 31) == 0 && nfg) atomicAdd(&sFg, nfg);
+        if (lane == 0 && nfg) atomicAdd(&B.s.img_cnt[4 * img + 1], nfg);
         if (!ok) set_status(B, d, ST_ITER);
-        __syncthreads();
-        if (threadIdx.x == 0 && sFg) atomicAdd(&B.s.img_cnt[4 * sImg + 1], sFg);
-        __syncthreads();
     }
 }
 
@@ -312,7 +303,6 @@ __device__ __forceinline__ int node_id_of_key(const Batch &B, const ImgDesc &d, 
 }
 
 __global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
-    __shared__ int sTile, sImg;
     // image totals
     for (int i = blockIdx.x * NTHREADS + threadIdx.x; i < B.n_img; i += gridDim.x * NTHREADS) {
         const ImgDesc &d = B.desc[i];
@@ -323,19 +313,15 @@ __global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
         d.counts[2] = n - nfg;
         if (n > d.cap) set_status(B, d, ST_CAPACITY);
     }
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const int t = atomicAdd(&B.s.work[2], 1);
-            sTile = t;
-            sImg = t < B.n_tiles ? B.s.tstat[t].w : -1;
-        }
-        __syncthreads();
-        const int t = sTile;
-        if (t >= B.n_tiles) break;
-        const ImgDesc &d = B.desc[sImg];
+    // one warp per tile: node ids and initial records of the final roots
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (NTHREADS / 32);
+    for (int t = blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5); t < B.n_tiles; t += nwarps) {
+        const TileHdr &h = B.s.thdr[t];
+        const ImgDesc &d = B.desc[h.img];
         const int nb = B.s.tstat[t].z;
-        const uint32_t slot0 = (uint32_t)(B.n_img + tile_geo(d, t - d.tile0, B.th).b);
-        for (int kb = threadIdx.x; kb < nb; kb += NTHREADS) {
+        const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
+        for (int kb = lane; kb < nb; kb += 32) {
             const uint32_t slot = slot0 + kb;
             const unsigned long long v = B.s.gp[slot];
             if ((uint32_t)v != slot) continue;
@@ -354,7 +340,6 @@ __global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
                 if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((B.s.binfo[slot] >> 16) & 1);
             }
         }
-        __syncthreads();
     }
 }
 
@@ -369,7 +354,8 @@ void launch_merge(const Batch &B, cudaStream_t st) {
 }
 
 void launch_resolve(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    k_resolve<<<min(B.n_tiles, 4 * c.sms), NTHREADS, 0, st>>>(B);
+    const int blocks = (B.n_tiles + NTHREADS / 32 - 1) / (NTHREADS / 32);
+    k_resolve<<<max(1, min(blocks, 8 * c.sms)), NTHREADS, 0, st>>>(B);
 }
 
 void launch_scan(const Batch &B, cudaStream_t st) {
@@ -380,7 +366,8 @@ void launch_scan(const Batch &B, cudaStream_t st) {
 }
 
 void launch_canon(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    k_canon<<<min(B.n_tiles, 4 * c.sms), NTHREADS, 0, st>>>(B);
+    const int blocks = (B.n_tiles + NTHREADS / 32 - 1) / (NTHREADS / 32);
+    k_canon<<<max(1, min(blocks, 8 * c.sms)), NTHREADS, 0, st>>>(B);
 }
 
 }  // namespace ccl
