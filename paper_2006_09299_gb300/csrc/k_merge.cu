@@ -34,10 +34,11 @@ enum { TOP, BOTTOM, LEFT, RIGHT };
 // Union-find slot of the border root that owns edge cell `pos` (a column for
 // TOP / BOTTOM, a row for LEFT / RIGHT) of tile lt.
 __device__ __forceinline__ uint32_t edge_slot(const Batch &B, const ImgDesc &d, int lt, int side, int pos) {
-    const TileGeo g = tile_geo(d, lt, B.th);
-    const int off = side == TOP ? edge_top(g, pos) : side == BOTTOM ? edge_bottom(g, pos)
-                  : side == LEFT ? edge_left(g, pos) : edge_right(g, pos);
-    return (uint32_t)(B.n_img + g.b) + B.s.edges[g.b + off];
+    const TileHdr &h = B.s.thdr[d.tile0 + lt];
+    const int64_t eb = h.b;
+    const int tw = h.tw;
+    const int off = side == TOP ? pos : side == BOTTOM ? tw + pos : side == LEFT ? 2 * tw + pos : 2 * tw + h.th + pos;
+    return (uint32_t)(B.n_img + eb) + B.s.edges[eb + off];
 }
 
 __device__ __forceinline__ uint32_t plane_word(const Batch &B, const ImgDesc &d, int y, int j) {
@@ -225,23 +226,27 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
 }
 
 // Node count of every segment (one tile row: 32 words of the node plane).
-__global__ void __launch_bounds__(NTHREADS) k_scan_count(Batch B) {
-    __shared__ int sPart[NWARPS];
+__global__ void __launch_bounds__(SCAN_B) k_scan_count(Batch B) {
+    __shared__ int sPart[SCAN_B / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t s0 = (int64_t)blockIdx.x * SCAN_B;
-    int acc = 0;
-    for (int k = warp; k < SCAN_B; k += NWARPS) {
-        const int64_t s = s0 + k;
-        if (s >= B.n_segs) break;
-        const int c = warp_sum(__popc(B.s.nodebits[s * WPR + lane]));
-        if (lane == 0) B.s.seg_cnt[s] = c;
-        acc += c;
+    const int64_t s = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+    int c = 0;
+    if (s < B.n_segs) {
+        // one segment per thread: its 32 words in eight independent vector loads
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(B.s.nodebits + s * WPR);
+        uint4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = w4[q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c += __popc(v[q].x) + __popc(v[q].y) + __popc(v[q].z) + __popc(v[q].w);
+        B.s.seg_cnt[s] = c;
     }
-    if (lane == 0) sPart[warp] = acc;
+    const int wsum = warp_sum(c);
+    if (lane == 0) sPart[warp] = wsum;
     __syncthreads();
     if (threadIdx.x == 0) {
         int tot = 0;
-        for (int k = 0; k < NWARPS; ++k) tot += sPart[k];
+        for (int k = 0; k < SCAN_B / 32; ++k) tot += sPart[k];
         B.s.blk_sum[blockIdx.x] = tot;
     }
 }
@@ -360,7 +365,7 @@ void launch_resolve(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
 
 void launch_scan(const Batch &B, cudaStream_t st) {
     const int nblk = (int)((B.n_segs + SCAN_B - 1) / SCAN_B);
-    k_scan_count<<<nblk, NTHREADS, 0, st>>>(B);
+    k_scan_count<<<nblk, SCAN_B, 0, st>>>(B);
     k_scan_blocks<<<1, 1024, 0, st>>>(B, nblk);
     k_scan_apply<<<nblk, SCAN_B, 0, st>>>(B);
 }
