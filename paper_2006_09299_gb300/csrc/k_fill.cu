@@ -171,20 +171,46 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
         int seg = (lane == 0 || kprev != key) ? lane : 0;
 #pragma unroll
         for (int dd = 1; dd < 32; dd <<= 1) seg = max(seg, __shfl_up_sync(FULL, seg, dd));
+        // sums of 32-bit values whose warp total also fits in 32 bits move
+        // through 32-bit shuffles (the usual case: small absorbed nodes)
+        const unsigned long long lim = 1ull << 27;   // 32 lanes x 2^27 < 2^32
+        if (__all_sync(FULL, v.area < lim && v.sx < lim && v.sy < lim)) {
+            uint32_t ar = (uint32_t)v.area, sxr = (uint32_t)v.sx, syr = (uint32_t)v.sy;
 #pragma unroll
-        for (int dd = 1; dd < 32; dd <<= 1) {
-            const unsigned long long a = __shfl_up_sync(FULL, v.area, dd), sx = __shfl_up_sync(FULL, v.sx, dd),
-                                     sy = __shfl_up_sync(FULL, v.sy, dd);
-            const int x0 = __shfl_up_sync(FULL, v.xmin, dd), y0 = __shfl_up_sync(FULL, v.ymin, dd),
-                      x1 = __shfl_up_sync(FULL, v.xmax, dd), y1 = __shfl_up_sync(FULL, v.ymax, dd);
-            if (lane - dd >= seg) {
-                v.area += a;
-                v.sx += sx;
-                v.sy += sy;
-                v.xmin = min(v.xmin, x0);
-                v.ymin = min(v.ymin, y0);
-                v.xmax = max(v.xmax, x1);
-                v.ymax = max(v.ymax, y1);
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const uint32_t a = __shfl_up_sync(FULL, ar, dd), sx = __shfl_up_sync(FULL, sxr, dd),
+                               sy = __shfl_up_sync(FULL, syr, dd);
+                const int x0 = __shfl_up_sync(FULL, v.xmin, dd), y0 = __shfl_up_sync(FULL, v.ymin, dd),
+                          x1 = __shfl_up_sync(FULL, v.xmax, dd), y1 = __shfl_up_sync(FULL, v.ymax, dd);
+                if (lane - dd >= seg) {
+                    ar += a;
+                    sxr += sx;
+                    syr += sy;
+                    v.xmin = min(v.xmin, x0);
+                    v.ymin = min(v.ymin, y0);
+                    v.xmax = max(v.xmax, x1);
+                    v.ymax = max(v.ymax, y1);
+                }
+            }
+            v.area = ar;
+            v.sx = sxr;
+            v.sy = syr;
+        } else {
+#pragma unroll
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const unsigned long long a = __shfl_up_sync(FULL, v.area, dd), sx = __shfl_up_sync(FULL, v.sx, dd),
+                                         sy = __shfl_up_sync(FULL, v.sy, dd);
+                const int x0 = __shfl_up_sync(FULL, v.xmin, dd), y0 = __shfl_up_sync(FULL, v.ymin, dd),
+                          x1 = __shfl_up_sync(FULL, v.xmax, dd), y1 = __shfl_up_sync(FULL, v.ymax, dd);
+                if (lane - dd >= seg) {
+                    v.area += a;
+                    v.sx += sx;
+                    v.sy += sy;
+                    v.xmin = min(v.xmin, x0);
+                    v.ymin = min(v.ymin, y0);
+                    v.xmax = max(v.xmax, x1);
+                    v.ymax = max(v.ymax, y1);
+                }
             }
         }
         const long long knext = __shfl_down_sync(FULL, key, 1);
