@@ -159,3 +159,18 @@ def test_results_alone_and_in_the_mix_are_identical():
         assert torch.equal(mix.parent[:n], alone.parent[:n])
         assert torch.equal(mix.features[:, :n], alone.features[:, :n])
         ctx.close()
+    # and the mix is the oracle's result, hole filling included
+    from oracle import reference as orc
+    for f, r in list(zip(frames, reqs))[:4]:
+        ref = orc.analyze(f, w=f.shape[1])
+        mix = r.result
+        n = mix.n
+        assert n == ref["n"]
+        np.testing.assert_array_equal(mix.fg.cpu().numpy(), ref["fg"])
+        np.testing.assert_array_equal(mix.bg.cpu().numpy(), ref["bg"])
+        np.testing.assert_array_equal(mix.parent[:n].cpu().numpy(), ref["parent"])
+        np.testing.assert_array_equal(mix.features[:, :n].cpu().numpy(), ref["feat"])
+        fmap, ff, fpar = orc.fill(ref, s.fill_threshold)
+        np.testing.assert_array_equal(mix.fill_map[:n].cpu().numpy(), fmap)
+        np.testing.assert_array_equal(mix.filled_features[:, :n].cpu().numpy(), ff)
+        np.testing.assert_array_equal(mix.filled_parent[:n].cpu().numpy(), fpar)
