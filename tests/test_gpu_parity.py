@@ -296,3 +296,30 @@ def test_uneven256_full_batch_as_benched(ccl):
             np.testing.assert_array_equal(o.filled_features[:, :n].cpu().numpy(), ff)
             np.testing.assert_array_equal(o.filled_parent[:n].cpu().numpy(), fpar)
     bctx.close()
+
+
+def test_sweep4096_full_batch_as_benched(ccl):
+    """All 25 images of the default bench workload (4096 x 4096, d in
+    {0.1..0.9} x g in {1..16}) in one batched call with hole filling 64, as
+    the bench times it, every image against the oracle."""
+    batch = [(inputs.sweep_image(i, j), 4096) for i in range(5) for j in range(5)]
+    imgs = [(to_dev(p), w) for p, w in batch]
+    bctx = ccl.BatchContext(len(batch), 25 * 4096 * 4096, 4096)
+    outs = bctx.new_outputs([(4096, 4096)] * len(batch), labels=True, fill=True)
+    for _ in range(2):
+        bctx.analyze(imgs, outs=outs)
+        bctx.fill_holes(64)
+    torch.cuda.synchronize()
+    for (p, w), o in zip(batch, outs):
+        r = run_oracle(p, w)
+        n = o.n
+        assert o.status() == 0 and n == r["n"]
+        np.testing.assert_array_equal(o.fg.cpu().numpy(), r["fg"])
+        np.testing.assert_array_equal(o.bg.cpu().numpy(), r["bg"])
+        np.testing.assert_array_equal(o.parent[:n].cpu().numpy(), r["parent"])
+        np.testing.assert_array_equal(o.features[:, :n].cpu().numpy(), r["feat"])
+        fmap, ff, fpar = orc.fill(r, 64)
+        np.testing.assert_array_equal(o.fill_map[:n].cpu().numpy(), fmap)
+        np.testing.assert_array_equal(o.filled_features[:, :n].cpu().numpy(), ff)
+        np.testing.assert_array_equal(o.filled_parent[:n].cpu().numpy(), fpar)
+    bctx.close()
