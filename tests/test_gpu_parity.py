@@ -83,14 +83,15 @@ SIZES = [(1, 1), (1, 2), (2, 1), (3, 40), (15, 17), (31, 33), (32, 32), (33, 102
          (65, 1025), (70, 2049), (100, 3000), (257, 1100), (40, 4100)]
 
 
+@pytest.mark.parametrize("conn", [0, 1])
 @pytest.mark.parametrize("kind", inputs.ADVERSARIAL_KINDS)
-def test_adversarial_shapes(ccl, kind):
+def test_adversarial_shapes(ccl, kind, conn):
     for h, w in SIZES:
         img = inputs.adversarial(h, w, kind)
         pitch = -(-w // 16) * 16
         padded = inputs.pitched(img, pitch)
-        g = run_single(ccl, padded, w, fills=(0, 3, INT64_MAX))
-        assert_parity(g, run_oracle(padded, w), fills=(0, 3, INT64_MAX))
+        g = run_single(ccl, padded, w, conn=conn, fills=(0, 3, INT64_MAX))
+        assert_parity(g, run_oracle(padded, w, conn), fills=(0, 3, INT64_MAX))
 
 
 @pytest.mark.parametrize("conn", [0, 1])
