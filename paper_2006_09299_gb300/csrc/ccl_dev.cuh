@@ -143,14 +143,6 @@ __device__ __forceinline__ uint32_t nz16(uint4 v) {
     return nz4(v.x) | (nz4(v.y) << 4) | (nz4(v.z) << 8) | (nz4(v.w) << 12);
 }
 
-__device__ __forceinline__ uint4 ld_stream16(const uint8_t *p) {
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
 // ------------------------------------- bulk copies into shared memory
 // One thread issues cp.async.bulk copies (global -> shared, 16-byte aligned,
 // sizes a multiple of 16) that complete on a shared-memory mbarrier; the
@@ -283,10 +275,6 @@ __device__ __forceinline__ TileGeo tile_geo(const ImgDesc &d, int lt, int TH) {
     return g;
 }
 
-__device__ __forceinline__ int edge_top(const TileGeo &g, int c) { return c; }
-__device__ __forceinline__ int edge_bottom(const TileGeo &g, int c) { return g.tw + c; }
-__device__ __forceinline__ int edge_left(const TileGeo &g, int r) { return 2 * g.tw + r; }
-__device__ __forceinline__ int edge_right(const TileGeo &g, int r) { return 2 * g.tw + g.th + r; }
 
 // Image owning flat tile t: the last image whose tile0 <= t.
 __device__ __forceinline__ int image_of_tile(const Batch &B, int t) {
