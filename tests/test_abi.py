@@ -87,3 +87,39 @@ def test_no_device_is_an_error_not_a_fallback(lib):
     h = ctypes.c_void_p()
     st = lib._lib.ccl_create(ctypes.byref(h), 64, 64, 64)
     assert st == lib.ERR_CUDA and not h.value
+
+
+C_DEMO = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c", "abi_demo.c")
+
+
+def build_c_demo(tmpdir):
+    """Compile the plain C caller and link it against libccl.so."""
+    import paper_2006_09299_gb300.build as b
+    cuda = os.path.dirname(os.path.dirname(b.nvcc())) if os.path.sep in b.nvcc() else "/usr/local/cuda"
+    exe = os.path.join(str(tmpdir), "abi_demo")
+    lib_dir = os.path.dirname(b.OUT)
+    cmd = ["gcc", "-std=c99", "-O1", "-I", HEADER_DIR, "-I", os.path.join(cuda, "include"), C_DEMO, "-o", exe,
+           "-L", lib_dir, "-lccl", "-Wl,-rpath," + lib_dir, "-L", os.path.join(cuda, "lib64"), "-lcudart",
+           "-Wl,-rpath," + os.path.join(cuda, "lib64")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return exe
+
+
+def test_plain_c_caller_links_and_reports_no_device(lib, tmp_path):
+    """A C program uses the ABI without Python; here (no GPU) ccl_create
+    answers CCL_ERR_CUDA and the program says so."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present: the GPU test runs the program")
+    exe = build_c_demo(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 2, r.stdout + r.stderr
+    assert "no device" in r.stdout
+
+
+@pytest.mark.gpu
+def test_plain_c_caller_on_gpu(lib, tmp_path):
+    exe = build_c_demo(tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
