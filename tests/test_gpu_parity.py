@@ -80,7 +80,7 @@ def assert_parity(g, r, labels=True, fills=()):
 
 
 SIZES = [(1, 1), (1, 2), (2, 1), (3, 40), (15, 17), (31, 33), (32, 32), (33, 1023), (64, 1024),
-         (65, 1025), (70, 2049), (100, 3000), (257, 1100), (40, 4100)]
+         (65, 1025), (70, 2049), (100, 3000), (257, 1100), (40, 4100), (2100, 7), (1000, 1)]
 
 
 @pytest.mark.parametrize("conn", [0, 1])
