@@ -231,7 +231,7 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, Plan *
         px += (int64_t)x.w * x.h;
         edges += 2 * (int64_t)x.w * d.TY + 2 * (int64_t)x.h * d.TX;
         ncap += d.ncap;
-        hi += (int64_t)(d.TY - 1) * d.TX * WPR;
+        hi += (int64_t)(d.TY - 1) * d.TX * WPR * H_SPLIT;
         vi += (int64_t)(d.TX - 1) * x.h;
         pi += 2 * (int64_t)d.TX * WPR + 2 * (int64_t)x.h;
     }

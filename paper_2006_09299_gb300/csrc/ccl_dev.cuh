@@ -29,6 +29,10 @@ constexpr int TH_MIN = 16;             // chosen per context (ccl_set_tile_rows)
 constexpr int TILE_PX = TH_MAX * TW;   // 32768: local pixel index fits 15 bits
 constexpr int NTHREADS = 256;          // threads of the write / resolve / canon kernels
 constexpr int NWARPS = NTHREADS / 32;
+// Horizontal tile-boundary merge items per word of the boundary row (each
+// takes 32 / H_SPLIT of the word's columns, so a dense boundary spreads its
+// unions over more threads).
+constexpr int H_SPLIT = 4;
 constexpr int SCAN_B = 256;            // segments per block of the node scan
 constexpr unsigned FULL = 0xFFFFFFFFu;
 

@@ -59,8 +59,12 @@ __device__ __forceinline__ uint32_t starts(uint32_t c, uint32_t cl, int j, uint3
 template <int CONN>
 __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool *ok) {
     const int64_t words = (int64_t)d.TX * WPR;
+    const int part = (int)(item % H_SPLIT);   // columns [part, part + 1) x 32 / H_SPLIT of the word
+    item /= H_SPLIT;
     const int bb = (int)(item / words);        // boundary between band bb and bb+1
     const int j = (int)(item - (int64_t)bb * words);
+    constexpr int SPAN = 32 / H_SPLIT;
+    const uint32_t range = ((1u << SPAN) - 1u) << (SPAN * part);
     const int x = 32 * j;
     if (x >= d.w) return;
     const int yu = (bb + 1) * B.th - 1, yd = yu + 1;
@@ -79,10 +83,10 @@ __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool 
     const uint32_t adr = CONN ? (~cdr & vmr) : cdr, aur = CONN ? (~cur & vmr) : cur;
     const uint32_t ad_prev = (ad << 1) | (j ? adl >> 31 : 0u), ad_next = (ad >> 1) | (adr << 31);
     const uint32_t au_prev = (au << 1) | (j ? aul >> 31 : 0u), au_next = (au >> 1) | (aur << 31);
-    const uint32_t va = ad & au & ((ed & ad) | (eu & au));
-    const uint32_t vb = bd & bu & ((ed & bd) | (eu & bu));
-    const uint32_t d1 = ad & ~au & au_next & ~ad_next;
-    const uint32_t d2 = ad & ~au & au_prev & ~ad_prev;
+    const uint32_t va = ad & au & ((ed & ad) | (eu & au)) & range;
+    const uint32_t vb = bd & bu & ((ed & bd) | (eu & bu)) & range;
+    const uint32_t d1 = ad & ~au & au_next & ~ad_next & range;
+    const uint32_t d2 = ad & ~au & au_prev & ~ad_prev & range;
     const int ltu = bb * d.TX, ltd = (bb + 1) * d.TX;   // first tile of each band
     uint32_t m = va | vb;
     while (m) {
