@@ -135,6 +135,27 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
     const int64_t total = (int64_t)B.n_img + B.s.seg_base[B.n_segs];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     ImageCursor cur;
+    // lane 31 carries its last group across iterations while the survivor
+    // repeats (the holes of one large component, scattered over the image)
+    long long ckey = -1;
+    int cimg = 0;
+    FeatAcc cv{0ull, 0ull, 0ull, INT32_MAX, INT32_MAX, -1, -1};
+    auto push = [&](long long k, int im, const FeatAcc &a) {
+        const ImgDesc &d = B.desc[im];
+        hash_push(H, d.filled_feat, d.cap, im, (int)(uint32_t)k, a);
+    };
+    auto push_or_carry = [&](long long k, int im, const FeatAcc &a) {
+        if (lane != 31) {
+            push(k, im, a);
+        } else if (k == ckey) {
+            acc_merge(cv, a);
+        } else {
+            if (ckey >= 0) push(ckey, cimg, cv);
+            ckey = k;
+            cimg = im;
+            cv = a;
+        }
+    };
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < total;
          base += warps * 32) {
         const int64_t f = base + lane;
@@ -162,10 +183,7 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
         if (!__any_sync(FULL, key >= 0)) continue;
         const long long kprev = __shfl_up_sync(FULL, key, 1);
         if (!__any_sync(FULL, key >= 0 && lane > 0 && kprev == key)) {
-            if (key >= 0) {
-                const ImgDesc &d = B.desc[img];
-                hash_push(H, d.filled_feat, d.cap, img, (int)(uint32_t)key, v);
-            }
+            if (key >= 0) push_or_carry(key, img, v);
             continue;
         }
         int seg = (lane == 0 || kprev != key) ? lane : 0;
@@ -214,11 +232,9 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
             }
         }
         const long long knext = __shfl_down_sync(FULL, key, 1);
-        if (key >= 0 && (lane == 31 || knext != key)) {
-            const ImgDesc &d = B.desc[img];
-            hash_push(H, d.filled_feat, d.cap, img, (int)(uint32_t)key, v);
-        }
+        if (key >= 0 && (lane == 31 || knext != key)) push_or_carry(key, img, v);
     }
+    if (ckey >= 0) push(ckey, cimg, cv);
     __syncthreads();
     hash_flush(H, B.desc, true);
 }
