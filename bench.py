@@ -489,6 +489,8 @@ def host_cpu():
     except OSError:
         pass
     import platform
+    parts = {"0xd4f": "Arm Neoverse V2 (Grace)", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    model = parts.get(model, model)
     return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
 
 
