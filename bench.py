@@ -579,6 +579,9 @@ def run_serve(args):
     srv.start()
     rows = []
     best = None
+    # resident slots for every frame size: enough for a full batch on every
+    # stream plus the one being admitted
+    srv.preallocate(sorted({be.size_key(f) for f in frames}), args.serve_batch * (args.serve_streams + 1))
     gc.collect()
     gc.disable()   # no collector pauses inside the latency measurement
     try:
@@ -766,7 +769,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep4096", choices=["sweep4096", "rings8192", "uneven256", "serve", "paper2048"])
     ap.add_argument("--paper-per-cell", type=int, default=4, help="paper2048: images per density x granularity cell")
-    ap.add_argument("--serve-rates", default="500,1000,2000,3000,4000,5000,6000,8000")
+    ap.add_argument("--serve-rates", default="500,1000,2000,4000,6000,8000,10000,12000,16000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-batch", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=2)

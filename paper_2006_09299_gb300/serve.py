@@ -124,6 +124,18 @@ class Server:
             self.waiting.popleft()
             self.admitted.append(r)
 
+    def preallocate(self, keys, per_key):
+        """Allocate up to `per_key` idle slots for each size key (within the
+        memory budget), so that bursts are not slowed by allocation."""
+        with self.lock:
+            for key in keys:
+                while len(self.free_slots[key]) < per_key:
+                    need = self.backend.slot_bytes(key)
+                    if self.used + need > self.budget:
+                        break
+                    self.free_slots[key].append(self.backend.alloc_slot(key))
+                    self.used += need
+
     def _evict_for(self, need):
         """Free idle slots of other size classes until `need` bytes fit."""
         freed = False
@@ -227,7 +239,7 @@ class GpuBackend:
     """Runs batches through the CUDA library on n_streams streams."""
 
     def __init__(self, n_streams=2, max_batch=16, max_side=3840, max_frame_px=3840 * 2160, device=0,
-                 capacity_fraction=16):
+                 capacity_fraction=16, stage_threads=4):
         import torch
         from . import ccl
         self.torch = torch
@@ -238,6 +250,11 @@ class GpuBackend:
         self.ctxs = [ccl.BatchContext(max_batch, max_batch * max_frame_px, max_side, graph_cache=False)
                      for _ in range(n_streams)]
         self.capacity_fraction = capacity_fraction
+        # frames are staged into their slots' pinned buffers by a few host
+        # threads (numpy copies release the interpreter lock), so the
+        # scheduler thread is not limited to one core's copy bandwidth
+        import concurrent.futures
+        self.stager = concurrent.futures.ThreadPoolExecutor(max_workers=stage_threads)
 
     @staticmethod
     def size_key(frame):
@@ -268,11 +285,18 @@ class GpuBackend:
     def launch(self, k, batch, fill_threshold):
         torch = self.torch
         st = self.streams[k]
+        def stage(r):
+            img, out, host, w = r.slot.handle
+            host.numpy()[:, :w] = r.frame
+        if len(batch) >= 4:
+            list(self.stager.map(stage, batch))
+        else:
+            for r in batch:
+                stage(r)
         with torch.cuda.stream(st):
             imgs, outs = [], []
             for r in batch:
                 img, out, host, w = r.slot.handle
-                host[:, :w].copy_(torch.from_numpy(r.frame))
                 img.copy_(host, non_blocking=True)
                 imgs.append((img, w))
                 outs.append(out)

@@ -174,3 +174,18 @@ def test_results_alone_and_in_the_mix_are_identical():
         np.testing.assert_array_equal(mix.fill_map[:n].cpu().numpy(), fmap)
         np.testing.assert_array_equal(mix.filled_features[:, :n].cpu().numpy(), ff)
         np.testing.assert_array_equal(mix.filled_parent[:n].cpu().numpy(), fpar)
+
+
+def test_preallocate_respects_budget_and_is_reused():
+    be = FakeBackend(nbytes=100)
+    s = Server(be, memory_budget=100 * 10 * 10 * 5, max_batch=4, n_streams=2)
+    s.preallocate([(10, 10), (20, 20)], per_key=3)
+    # 3 slots of 10x10 (10000 bytes each) fit; a 20x20 slot (40000) does not
+    # fit in the 20000 bytes left of the 50000 budget
+    assert len(s.free_slots[(10, 10)]) == 3
+    assert len(s.free_slots[(20, 20)]) == 0
+    assert s.used == 30000 <= s.budget
+    allocated = be.alloc
+    r = s.submit(np.zeros((10, 10), np.uint8))
+    s.step()
+    assert r.slot is not None and be.alloc == allocated   # an idle slot was reused
