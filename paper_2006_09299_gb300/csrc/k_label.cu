@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             }
             const uint32_t vr = r < th ? vm : 0u;
             sC[r][lane] = word;
+            sB[r][lane] = 0;
             if (r < th) B.s.fgbits[plane0 + r * rowwords + lane] = word;
             const uint32_t left = __shfl_up_sync(FULL, word, 1);
             const uint32_t prev = (word << 1) | (lane ? (left >> 31) : 0u);
@@ -363,12 +364,12 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             }
             sR[r][lane] = roots;
             sMul[r][lane] = mul;
-            sB[r][lane] = 0;
         }
-        __syncthreads();
 
         // ---- roots of the edge cells are border roots (on the top and
-        // bottom rows one cell per run is enough: the one where it starts)
+        // bottom rows one cell per run is enough: the one where it starts).
+        // This runs alongside the closure: its finds read parents that the
+        // closure only ever replaces by the same roots.
         const int nedge = 2 * tw + 2 * th;
         for (int i = threadIdx.x; i < nedge; i += LABEL_THREADS) {
             int r, c;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             else if (i < 2 * tw + th) { r = i - 2 * tw; c = 0; }
             else { r = i - 2 * tw - th; c = tw - 1; }
             if (i < 2 * tw && !((sE[r][c >> 5] >> (c & 31)) & 1u)) continue;
-            const int root = par[swz(r * TW + run_start_col(sE, sRS, r, c))];
+            const int root = local_find(par, r * TW + run_start_col(sE, sRS, r, c), &ok);
             atomicOr(&sB[root >> 10][(root >> 5) & 31], 1u << (root & 31));
         }
         __syncthreads();
