@@ -24,20 +24,23 @@ namespace ccl {
 // their features in on-chip records (more spill to global atomics); a
 // single-run root's features are those of its run, written when the run is
 // seen. Node ids of the first MAXID roots are kept on chip.
-constexpr int MAXR = 2048;
-constexpr int MAXID = 3584;
+// (per tile height: a 16-row tile has half the pixels)
+template <int TH> struct WriteCfg;
+template <> struct WriteCfg<32> { static constexpr int MAXR = 2048, MAXID = 3584, THREADS = 256, CTAS = 2; };
+template <> struct WriteCfg<16> { static constexpr int MAXR = 1024, MAXID = 1792, THREADS = 128, CTAS = 4; };
 
 // Per record: S, Sx, Sy, xmin, xmax and the row mask, all updated with
 // native 32-bit shared reductions (a packed 64-bit sum was slower).
 constexpr int REC_BYTES = 6 * 4;
 
-// Two 256-thread CTAs per SM (16 warps): while one waits on its tile's
-// global reads the other streams label rows.
-constexpr int WRITE_THREADS = 256;
+// Several CTAs per SM (16 warps in all): while one waits on its tile's
+// global reads the others stream label rows. 32-row tiles: two 256-thread
+// CTAs; 16-row tiles: four 128-thread CTAs with half the on-chip records.
 
 template <int TH>
 constexpr size_t write_smem() {
-    return (size_t)MAXR * REC_BYTES + (size_t)MAXID * 4 + MAXID / 8 + (size_t)(WRITE_THREADS / 32) * TW * 4 +
+    constexpr int MAXR = WriteCfg<TH>::MAXR, MAXID = WriteCfg<TH>::MAXID;
+    return (size_t)MAXR * REC_BYTES + (size_t)MAXID * 4 + MAXID / 8 + (size_t)(WriteCfg<TH>::THREADS / 32) * TW * 4 +
            3 * TH * WPR * 4 + 2 * TH * WPR * 2;
 }
 
@@ -90,8 +93,9 @@ __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e)
 }
 
 template <int TH>
-__global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
-    constexpr int NTHREADS = WRITE_THREADS;
+__global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_write(Batch B) {
+    constexpr int MAXR = WriteCfg<TH>::MAXR, MAXID = WriteCfg<TH>::MAXID;
+    constexpr int NTHREADS = WriteCfg<TH>::THREADS;
     constexpr int NWARPS = NTHREADS / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     // feature records of the local roots, structure of arrays (tile-local x, y)
@@ -558,9 +562,9 @@ __global__ void __launch_bounds__(WRITE_THREADS, 2) k_write(Batch B) {
 
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     if (B.th == 32)
-        k_write<32><<<min(B.n_tiles, 2 * c.sms), WRITE_THREADS, write_smem<32>(), st>>>(B);
+        k_write<32><<<min(B.n_tiles, WriteCfg<32>::CTAS * c.sms), WriteCfg<32>::THREADS, write_smem<32>(), st>>>(B);
     else
-        k_write<16><<<min(B.n_tiles, 2 * c.sms), WRITE_THREADS, write_smem<16>(), st>>>(B);
+        k_write<16><<<min(B.n_tiles, WriteCfg<16>::CTAS * c.sms), WriteCfg<16>::THREADS, write_smem<16>(), st>>>(B);
 }
 
 cudaError_t configure_write() {
