@@ -214,6 +214,13 @@ ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stre
 ccl_status ccl_filter_components_batched(ccl_ctx *ctx, int32_t target, int64_t area_threshold,
                                          ccl_stream_t stream);
 
+/* ccl_relabel_filtered for the images of the last batch: host arrays of n
+ * device pointers (n = the batch's image count), entry i for image i; a
+ * NULL pair skips the image. An image needs label images and fill buffers
+ * in its descriptor (CCL_ERR_STATE otherwise). */
+ccl_status ccl_relabel_filtered_batched(ccl_ctx *ctx, int32_t *const *d_fg_out, int32_t *const *d_bg_out,
+                                        ccl_stream_t stream);
+
 /* Tile height for later analyses of this context: 32 rows (default) or 16
  * rows of 1024 columns. Results are identical; the speed differs with the
  * image (ccl.autotune picks one per size class by timing both). */

@@ -48,6 +48,7 @@ SIGNATURES = {
     "ccl_relabel_filtered": (ctypes.c_int, [_p, _p, _p, _p]),
     "ccl_get_euler": (ctypes.c_int, [_p, ctypes.POINTER(_i64)]),
     "ccl_filter_components_batched": (ctypes.c_int, [_p, _i32, _i64, _p]),
+    "ccl_relabel_filtered_batched": (ctypes.c_int, [_p, _p, _p, _p]),
     "ccl_get_counts": (ctypes.c_int, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "ccl_create_batched": (ctypes.c_int, [ctypes.POINTER(_p), _i32, _i64, _i32]),
     "ccl_analyze_batched": (ctypes.c_int, [_p, ctypes.POINTER(ImageDesc), _i32, _p]),
@@ -264,6 +265,14 @@ class BatchContext(_Instrumented):
     def filter_components(self, target, area_threshold, stream=None):
         _check(_lib.ccl_filter_components_batched(self._h, int(target), int(area_threshold), _stream(stream)),
                "ccl_filter_components_batched")
+
+    def relabel_filtered(self, fg_outs, bg_outs, stream=None):
+        """Label images through the fill / filter map, one (fg, bg) pair of
+        int32 tensors per image of the last batch (None skips an image)."""
+        n = len(fg_outs)
+        fa = (_p * n)(*[_ptr(t) for t in fg_outs])
+        ba = (_p * n)(*[_ptr(t) for t in bg_outs])
+        _check(_lib.ccl_relabel_filtered_batched(self._h, fa, ba, _stream(stream)), "ccl_relabel_filtered_batched")
 
     def close(self):
         if self._h:

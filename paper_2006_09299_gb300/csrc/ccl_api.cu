@@ -474,6 +474,27 @@ ccl_status ccl_relabel_filtered(ccl_ctx *ctx, int32_t *d_fg_out, int32_t *d_bg_o
     return from_cuda(cudaGetLastError());
 }
 
+ccl_status ccl_relabel_filtered_batched(ccl_ctx *ctx, int32_t *const *d_fg_out, int32_t *const *d_bg_out,
+                                        ccl_stream_t stream) {
+    if (!ctx || !ctx->batched || !d_fg_out || !d_bg_out) return CCL_ERR_ARG;
+    if (!ctx->have_last) return CCL_ERR_STATE;
+    Plan P = ctx->last;
+    for (size_t i = 0; i < P.d.size(); ++i) {
+        ImgDesc &d = P.d[i];
+        if ((d_fg_out[i] == nullptr) != (d_bg_out[i] == nullptr)) return CCL_ERR_ARG;
+        if (d_fg_out[i] && (!d.fill_map || !d.fg)) return CCL_ERR_STATE;
+        d.fg_out = d_fg_out[i];
+        d.bg_out = d_bg_out[i];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = upload_plan(ctx, P, st);
+    if (e != cudaSuccess) return CCL_ERR_CUDA;
+    launch_relabel(make_batch(ctx, P), LaunchCfg{g_sms}, st);
+    ctx->launches += 1;
+    ctx->last_stream = st;
+    return from_cuda(cudaGetLastError());
+}
+
 ccl_status ccl_get_euler(ccl_ctx *ctx, int64_t *euler) {
     if (!ctx || !euler) return CCL_ERR_ARG;
     int32_t n = 0, nf = 0, nb = 0;

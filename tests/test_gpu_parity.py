@@ -256,7 +256,18 @@ def test_filter_batched_objects(ccl):
     bctx = ccl.BatchContext(len(batch), tot, 1200)
     outs = bctx.analyze(imgs, fill=True)
     bctx.filter_components(ccl.TARGET_OBJECTS, 12)
+    fg_outs = [torch.empty_like(o.fg) for o in outs]
+    bg_outs = [torch.empty_like(o.bg) for o in outs]
+    fg_outs[3] = bg_outs[3] = None   # an image may be skipped
+    bctx.relabel_filtered(fg_outs, bg_outs)
     torch.cuda.synchronize()
+    for i, ((p, w), o) in enumerate(zip(batch, outs)):
+        if fg_outs[i] is None:
+            continue
+        r = run_oracle(p, w)
+        efg, ebg = orc.relabel(r, orc.fill(r, 12, target_fg=1)[0])
+        np.testing.assert_array_equal(fg_outs[i].cpu().numpy(), efg)
+        np.testing.assert_array_equal(bg_outs[i].cpu().numpy(), ebg)
     for (p, w), o in zip(batch, outs):
         r = run_oracle(p, w)
         n = o.n
