@@ -22,9 +22,11 @@ namespace ccl {
 // Root ordinals of a tile put the roots of components with several runs
 // first, then the single-run roots. Multi-run roots below MAXR accumulate
 // their features in on-chip records (more spill to global atomics); a
-// single-run root's features are those of its run, written when the run is
-// seen. Node ids of the first MAXID roots are kept on chip.
-// (per tile height: a 16-row tile has half the pixels)
+// single-run root's features are those of its run, read back from the bit
+// planes in the feature pass. Node ids of the first MAXID roots are kept on
+// chip. Launch shape per tile height: several CTAs per SM (16 warps in all),
+// so that while one waits on its tile's global reads the others stream label
+// rows; 16-row tiles have half the pixels and half the records.
 template <int TH> struct WriteCfg;
 template <> struct WriteCfg<32> { static constexpr int MAXR = 2048, MAXID = 3584, THREADS = 256, CTAS = 2; };
 template <> struct WriteCfg<16> { static constexpr int MAXR = 1024, MAXID = 1792, THREADS = 128, CTAS = 4; };
@@ -32,10 +34,6 @@ template <> struct WriteCfg<16> { static constexpr int MAXR = 1024, MAXID = 1792
 // Per record: S, Sx, Sy, xmin, xmax and the row mask, all updated with
 // native 32-bit shared reductions (a packed 64-bit sum was slower).
 constexpr int REC_BYTES = 6 * 4;
-
-// Several CTAs per SM (16 warps in all): while one waits on its tile's
-// global reads the others stream label rows. 32-row tiles: two 256-thread
-// CTAs; 16-row tiles: four 128-thread CTAs with half the on-chip records.
 
 template <int TH>
 constexpr size_t write_smem() {
