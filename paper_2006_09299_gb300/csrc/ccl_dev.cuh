@@ -220,16 +220,6 @@ __device__ __forceinline__ uint32_t warp_excl_sum_u32(uint32_t v, uint32_t *tota
     return x - v;
 }
 
-__device__ __forceinline__ int warp_incl_max(int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, v, o);
-        if (lane >= o) v = max(v, y);
-    }
-    return v;
-}
-
 // Minimum over lanes strictly above this one (big when none).
 __device__ __forceinline__ int warp_suffix_min_excl(int v, int none) {
     const int lane = threadIdx.x & 31;

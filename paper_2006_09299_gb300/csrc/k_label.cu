@@ -130,24 +130,39 @@ __device__ __forceinline__ void contact_masks(const uint32_t (*sC)[WPR], const u
     *m2 = ac & ~au & au_prev & ~ac_prev;   // (r,x)-(r-1,x-1)
 }
 
-// Union the runs of each contact in bits `range` of word l of boundary r
-// (row r with row r - 1); the union by minimum of Algorithm 2.
+// Union the runs of each contact in word l of boundary r (row r with row
+// r - 1); the union by minimum of Algorithm 2. The run starts of the lane's
+// own word in both rows are kept in registers; only a diagonal partner in a
+// neighbouring word is looked up in shared memory.
 __device__ __forceinline__ void unite_contacts(uint32_t *par, const uint32_t (*sE)[WPR], const uint16_t (*sRS)[WPR],
-                                               int r, int l, uint32_t mv, uint32_t m1, uint32_t m2, uint32_t range,
-                                               bool *ok) {
-    uint32_t m = (mv | m1) & range;   // disjoint sets of pixels
+                                               int r, int l, uint32_t mv, uint32_t m1, uint32_t m2, bool *ok) {
+    const uint32_t ec = sE[r][l], eu = sE[r - 1][l];
+    const int rowc = r * TW, rowu = (r - 1) * TW;
+    const int cover_c = rowc + sRS[r][l], cover_u = rowu + sRS[r - 1][l];   // runs covering bit 0
+    const int word_c = rowc + 32 * l + 31, word_u = rowu + 32 * l + 31;
+    // run start (tile-local index) of the run holding bit b of word l
+    auto start_c = [&](int b) {
+        const uint32_t m = ec & mask_le(b);
+        return m ? word_c - __clz(m) : cover_c;
+    };
+    auto start_u = [&](int b) {
+        const uint32_t m = eu & mask_le(b);
+        return m ? word_u - __clz(m) : cover_u;
+    };
+    uint32_t m = mv | m1;   // disjoint sets of pixels
     while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        const int x = 32 * l + b;
-        const int xu = ((m1 >> b) & 1u) ? x + 1 : x;
-        local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, xu), ok);
+        const int bu = b + (int)((m1 >> b) & 1u);   // partner bit in the row above
+        const int u = bu < 32 ? start_u(bu) : rowu + run_start_col(sE, sRS, r - 1, 32 * l + 32);
+        local_union(par, start_c(b), u, ok);
     }
-    m = m2 & range;
+    m = m2;   // partner up-left
     while (m) {
-        const int x = 32 * l + __ffs(m) - 1;
+        const int b = __ffs(m) - 1;
         m &= m - 1;
-        local_union(par, r * TW + run_start_col(sE, sRS, r, x), (r - 1) * TW + run_start_col(sE, sRS, r - 1, x - 1), ok);
+        const int u = b > 0 ? start_u(b - 1) : rowu + run_start_col(sE, sRS, r - 1, 32 * l - 1);
+        local_union(par, start_c(b), u, ok);
     }
 }
 
@@ -157,8 +172,9 @@ constexpr uint32_t PAR_TAG = 0x80000000u;
 
 // One CTA per tile at a time, one warp per tile row. The image rows of the
 // next tile are fetched by bulk copies into a staging buffer while the CTA
-// works on the current one: the last warp's lane 0 claims tiles from the
-// work counter one tile ahead and issues the copies as soon as the staging
+// works on the current one: the last warp claims tiles from the work counter
+// one tile ahead, loads the claimed tile's copy record during the tile
+// before, and issues the copies (one row per lane) as soon as the staging
 // buffer has been read.
 //
 // Root ordinals: the roots of components with more than one run come first
@@ -184,48 +200,62 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
     uint16_t(*sSPre)[WPR] = sMPre + TH;                                  // single-run roots
     uint16_t(*sBPre)[WPR] = sSPre + TH;                                  // border roots
     uint8_t *stage = (uint8_t *)(sBPre + TH);                            // TH image rows
-    // per row, then prefixes over rows: runs | run-root slots << 16,
-    // multi-run roots | single-run roots << 16, border roots
+    // per row: runs | run-root slots << 16, multi-run roots | single-run
+    // roots << 16, border roots (each warp scans them for its row's prefix)
     __shared__ uint32_t sRowTot[3][TH];
-    __shared__ uint32_t sTot[3];
     __shared__ bool sRounds[TH];
-    __shared__ int sNext, sFg, sOk, sAbort;
+    __shared__ int sNext, sFg[2], sOk[2], sAbort;
     __shared__ __align__(8) uint64_t sBar;
     __shared__ TileHdr sHdr[2];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool issuer = threadIdx.x == LABEL_THREADS - 32;
-    // issuer: copy the rows and the header of tile tn into the staging
-    // buffer and header slot `slot`
-    auto stage_tile = [&](int tn, int slot) {
-        const int4 rec = B.s.tsrc[tn];
+    const bool issuer = warp == LABEL_WARPS - 1;   // the whole last warp stages tiles
+    // issuer warp: copy the rows (lane r: row r) and the header (lane 0) of
+    // tile tn, whose copy record is rec, into the staging buffer and header
+    // slot `slot`
+    auto stage_tile = [&](int tn, int slot, int4 rec) {
         const uint8_t *src = (const uint8_t *)(((uint64_t)(uint32_t)rec.y << 32) | (uint32_t)rec.x);
         const int rows = rec.w & 0xFF, bytes = rec.w >> 8;
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&sBar, (uint32_t)(rows * bytes + sizeof(TileHdr)));
-        bulk_g2s(&sHdr[slot], B.s.thdr + tn, (uint32_t)sizeof(TileHdr), &sBar);
-        for (int r = 0; r < rows; ++r) bulk_g2s(stage + r * TW, src + (int64_t)r * rec.z, (uint32_t)bytes, &sBar);
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&sBar, (uint32_t)(rows * bytes + sizeof(TileHdr)));
+            bulk_g2s(&sHdr[slot], B.s.thdr + tn, (uint32_t)sizeof(TileHdr), &sBar);
+        }
+        __syncwarp();
+        if (lane < rows) {
+            fence_proxy_async_smem();
+            bulk_g2s(stage + lane * TW, src + (int64_t)lane * rec.z, (uint32_t)bytes, &sBar);
+        }
     };
     if (threadIdx.x == 0) {
         mbar_init(&sBar, 1);
         sAbort = 0;
+        sFg[0] = sFg[1] = 0;
+        sOk[0] = sOk[1] = 1;
     }
     __syncthreads();
-    int claim = 0;   // issuer: the tile claimed for the iteration after next
+    int claim = 0;        // issuer: the tile claimed for the iteration after next
+    int4 rec_next{};      // issuer: its copy record, loaded during the tile before
     if (issuer) {
-        const int t0 = atomicAdd(&B.s.work[0], 1);
-        if (t0 < B.n_tiles) stage_tile(t0, 0);
-        sNext = t0;
-        claim = atomicAdd(&B.s.work[0], 1);
-    }
-    uint32_t phase = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            sFg = 0;
-            sOk = 1;
+        int t0 = 0, t1 = 0;
+        if (lane == 0) {
+            t0 = atomicAdd(&B.s.work[0], 1);
+            t1 = atomicAdd(&B.s.work[0], 1);
         }
-        __syncthreads();
-        const int t = sNext;
+        t0 = __shfl_sync(FULL, t0, 0);
+        t1 = __shfl_sync(FULL, t1, 0);
+        if (t0 < B.n_tiles) stage_tile(t0, 0, B.s.tsrc[t0]);
+        if (t1 < B.n_tiles) rec_next = B.s.tsrc[t1];
+        if (lane == 0) sNext = t0;
+        claim = t1;
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    // Per-tile counters alternate between two slots, so that thread 0 can
+    // read and reset the slot of one tile while the others start the next:
+    // the loop needs no barrier at its top or end.
+    for (int q = 0;; q ^= 1) {
+        const int t = sNext;   // written before the previous tile's last barrier
         if (t >= B.n_tiles) break;
         const bool staged = mbar_wait(&sBar, phase);
         if (!staged) atomicOr(&sAbort, 1);
@@ -256,16 +286,18 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             const uint32_t prev = (word << 1) | (lane ? (left >> 31) : 0u);
             const uint32_t e = ((word ^ prev) | (lane == 0 ? 1u : 0u)) & vr;
             sE[r][lane] = e;
-            const int last = e ? 32 * lane + 31 - __clz(e) : -1;
-            const int incl = warp_incl_max(last);
-            int excl = __shfl_up_sync(FULL, incl, 1);
-            if (lane == 0) excl = 0;
-            sRS[r][lane] = (unsigned short)((e & 1u) ? 32 * lane : max(excl, 0));
+            // the run covering bit 0 starts at the last run start of the
+            // words before (the highest earlier lane with a start)
+            const uint32_t before = __ballot_sync(FULL, e != 0u) & mask_lt(lane);
+            const int j = before ? 31 - __clz(before) : 0;
+            const uint32_t ej = __shfl_sync(FULL, e, j);
+            sRS[r][lane] = (unsigned short)((e & 1u) ? 32 * lane : (before ? 32 * j + 31 - __clz(ej) : 0));
             int tot;
             const int pre = warp_excl_sum(__popc(e), &tot);
             sRunPre[r][lane] = (unsigned short)pre;
             const bool rounds = rr_rounds(tw, tot);
-            const int slots = rounds ? 32 * __shfl_sync(FULL, warp_incl_max(__popc(e)), 31) : tot;
+            const int most = (int)__reduce_max_sync(FULL, (unsigned)__popc(e));
+            const int slots = rounds ? 32 * most : tot;
             if (lane == 0) {
                 sRowTot[0][r] = (uint32_t)tot | ((uint32_t)slots << 16);
                 sRounds[r] = rounds;
@@ -292,10 +324,12 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
         // the staging buffer and the other header slot are free: fetch the
         // next tile
         if (issuer) {
-            const int tn = claim;
-            if (tn < B.n_tiles) stage_tile(tn, (int)phase);
-            sNext = tn;
-            claim = atomicAdd(&B.s.work[0], 1);
+            const int tn = __shfl_sync(FULL, claim, 0);
+            if (tn < B.n_tiles) stage_tile(tn, (int)phase, rec_next);
+            if (lane == 0) {
+                sNext = tn;
+                claim = atomicAdd(&B.s.work[0], 1);
+            }
         }
 
         // ---- contacts of every row with the row above (Algorithm 2)
@@ -312,7 +346,7 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             sMV[r][lane] = mv;
             sM1[r][lane] = m1;
             sM2[r][lane] = m2;
-            if (mv | m1 | m2) unite_contacts(par, sE, sRS, r, lane, mv, m1, m2, FULL, &ok);
+            if (mv | m1 | m2) unite_contacts(par, sE, sRS, r, lane, mv, m1, m2, &ok);
         }
         __syncthreads();
 
@@ -383,6 +417,12 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
         }
         __syncthreads();
 
+        // the claim issued above has returned by now: fetch its copy record
+        if (issuer) {
+            const int tn = __shfl_sync(FULL, claim, 0);
+            if (tn < B.n_tiles) rec_next = B.s.tsrc[tn];
+        }
+
         // ---- ordinals of roots and border roots in raster order
         for (int r = warp; r < TH; r += LABEL_WARPS) {
             const uint32_t rm = sR[r][lane], mul = sMul[r][lane];
@@ -399,29 +439,27 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             }
         }
         __syncthreads();
-        if (warp == 0) {
+        // every warp scans the row totals itself (its own row's prefix is all
+        // it needs), which saves a barrier
+        uint32_t rbase[3], rtot[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                uint32_t tot;
-                const uint32_t ex = warp_excl_sum_u32(lane < TH ? sRowTot[k][lane] : 0u, &tot);
-                if (lane < TH) sRowTot[k][lane] = ex;
-                if (lane == 0) sTot[k] = tot;
-            }
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t ex = warp_excl_sum_u32(lane < TH ? sRowTot[k][lane] : 0u, &rtot[k]);
+            rbase[k] = __shfl_sync(FULL, ex, warp & 31);
         }
-        __syncthreads();
 
         // ---- per root: record, border slot, ordinal into par[root]
-        if (threadIdx.x == 0) B.s.tstat[t] = make_int4((int)(sTot[0] & 0xFFFFu), (int)sTot[1], (int)sTot[2], img);
+        if (threadIdx.x == 0) B.s.tstat[t] = make_int4((int)(rtot[0] & 0xFFFFu), (int)rtot[1], (int)rtot[2], img);
         uint16_t *rr = B.s.run_root + h.px;
         uint32_t *ri = B.s.rootinfo + h.px;
         const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
-        const int n_multi = (int)(sTot[1] & 0xFFFFu);
+        const int n_multi = (int)(rtot[1] & 0xFFFFu);
         int nfg = 0;
         for (int r = warp; r < th; r += LABEL_WARPS) {
             const uint32_t rm = sR[r][lane], bm = sB[r][lane], c = sC[r][lane], mul = sMul[r][lane];
-            int km = (int)(sRowTot[1][r] & 0xFFFFu) + sMPre[r][lane];
-            int ks = n_multi + (int)(sRowTot[1][r] >> 16) + sSPre[r][lane];
-            int kb = (int)sRowTot[2][r] + sBPre[r][lane];
+            int km = (int)(rbase[1] & 0xFFFFu) + sMPre[r][lane];
+            int ks = n_multi + (int)(rbase[1] >> 16) + sSPre[r][lane];
+            int kb = (int)rbase[2] + sBPre[r][lane];
             uint32_t m = rm;
             while (m) {
                 const int b = __ffs(m) - 1;
@@ -451,7 +489,7 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
         // ---- per run: root ordinal; per edge cell: border ordinal of its root
         for (int r = warp; r < th; r += LABEL_WARPS) {
             const bool rounds = sRounds[r];
-            const int row_slot = (int)(sRowTot[0][r] >> 16), pre = sRunPre[r][lane];
+            const int row_slot = (int)(rbase[0] >> 16), pre = sRunPre[r][lane];
             uint32_t m = sE[r][lane];
             int j = 0;
             while (m) {
@@ -475,14 +513,15 @@ __global__ void __launch_bounds__(TH * 32, TH == 32 ? 1 : 2) k_label(Batch B) {
             eg[i] = (uint16_t)((v >> 15) & 0xFFFu);
         }
         nfg = warp_sum(nfg);
-        if (lane == 0 && nfg) atomicAdd(&sFg, nfg);
-        if (!ok) atomicAnd(&sOk, 0);
+        if (lane == 0 && nfg) atomicAdd(&sFg[q], nfg);
+        if (!ok) atomicAnd(&sOk[q], 0);
         __syncthreads();
         if (threadIdx.x == 0) {
-            if (sFg) atomicAdd(&B.s.img_cnt[4 * img + 1], sFg);
-            if (!sOk) set_status(B, d, ST_ITER);
+            if (sFg[q]) atomicAdd(&B.s.img_cnt[4 * img + 1], sFg[q]);
+            if (!sOk[q]) set_status(B, d, ST_ITER);
+            sFg[q] = 0;   // the slot is next used two tiles on
+            sOk[q] = 1;
         }
-        __syncthreads();
     }
 }
 

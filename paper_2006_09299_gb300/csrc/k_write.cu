@@ -111,9 +111,10 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
     uint32_t(*sNB)[WPR] = sE + TH;
     uint16_t(*sRunPre)[WPR] = (uint16_t(*)[WPR])(sNB + TH);
     uint16_t(*sNBPre)[WPR] = sRunPre + TH;
-    __shared__ int sRowN[TH], sRowSeg[TH], sRowSlot[TH];   // runs, first node, first run-root slot
+    __shared__ int sRowN[TH], sRowSeg[TH], sRowSlot[TH];   // runs, first node, run-root slots
+    __shared__ int sRowBase[TH];                           // first run-root slot
     __shared__ bool sRounds[TH];
-    __shared__ int sT[2], sOk, sCap, sAbort;
+    __shared__ int sT[2], sOk[2], sCap[2], sAbort;
     __shared__ TileHdr sHdr[2];
     __shared__ int4 sSt[2];
     __shared__ __align__(8) uint64_t sHBar;
@@ -136,6 +137,8 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
     if (threadIdx.x == 0) {
         mbar_init(&sHBar, 1);
         sAbort = 0;
+        sOk[0] = sOk[1] = 1;
+        sCap[0] = sCap[1] = 0;
     }
     __syncthreads();
     int claim = 0;
@@ -143,14 +146,13 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
         fetch(atomicAdd(&B.s.work[3], 1), 0);
         claim = atomicAdd(&B.s.work[3], 1);
     }
+    __syncthreads();
     uint32_t phase = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            sOk = 1;
-            sCap = 0;
-        }
-        __syncthreads();
-        const int t = sT[phase];
+    // Per-tile flags alternate between two slots, so that thread 0 can read
+    // and reset the slot of one tile while the others start the next: the
+    // loop needs no barrier at its top or end.
+    for (int q = 0;; q ^= 1) {
+        const int t = sT[phase];   // written before the previous tile's barriers
         if (t >= B.n_tiles) break;
         if (!mbar_wait(&sHBar, phase)) atomicOr(&sAbort, 1);
         __syncthreads();
@@ -201,6 +203,14 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             }
         }
         const int seg_first = lane == 0 ? B.s.seg_base[h.seg0] : 0;
+        // node ids of the tile's border roots (their slots are consecutive),
+        // fetched while the planes are scanned; the run buffers hold them
+        // until the rows reuse that memory
+        int32_t *sBid = sRid;
+        for (int kb = threadIdx.x; kb < st.z; kb += NTHREADS) {
+            const uint32_t root = (uint32_t)B.s.gp[slot0 + kb];
+            sBid[kb] = root < (uint32_t)n_img ? 0 : B.s.canon[root];
+        }
 #pragma unroll
         for (int i = 0; i < RPW; ++i) {
             const int r = warp + i * NWARPS;
@@ -215,7 +225,8 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             int tot;
             sRunPre[r][lane] = (uint16_t)warp_excl_sum(__popc(e), &tot);
             const bool rounds = rr_rounds(tw, tot);
-            const int slots = rounds ? 32 * __shfl_sync(FULL, warp_incl_max(__popc(e)), 31) : tot;
+            const int most = (int)__reduce_max_sync(FULL, (unsigned)__popc(e));
+            const int slots = rounds ? 32 * most : tot;
             if (lane == 0) {
                 sRowN[r] = tot;
                 sRowSlot[r] = slots;
@@ -226,14 +237,25 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             if (lane == 0) sRowSeg[r] = r < th ? segw[i] - seg_first : 0;
         }
         __syncthreads();
-        if (warp == 0) {
+        {
+            // every warp scans the slot counts itself and keeps the prefixes
+            // of its own rows (saves a barrier)
             int tot;
             const int es = warp_excl_sum(lane < TH ? sRowSlot[lane] : 0, &tot);
-            if (lane < TH) sRowSlot[lane] = es;
+            if (lane < TH && lane % NWARPS == warp) sRowBase[lane] = es;
+            __syncwarp();
         }
-        __syncthreads();
 
-        // node id of a local root
+        // node id of a local root; the border roots' ids are in sBid until
+        // the rows phase
+        auto root_id_early = [&](uint32_t info) -> int {
+            const int idx = info & 0xFFFF;
+            if (!((info >> 17) & 1u)) {
+                const int r = idx >> 10, c = idx & 1023, l = c >> 5;
+                return 1 + sRowSeg[r] + sNBPre[r][l] + __popc(sNB[r][l] & mask_lt(c & 31));
+            }
+            return sBid[(info >> 18) & 0xFFFu];
+        };
         auto root_id = [&](uint32_t info) -> int {
             const int idx = info & 0xFFFF;
             if (!((info >> 17) & 1u)) {
@@ -255,7 +277,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             const bool multi = k < n_multi;
             const bool spill = valid && multi && k >= MAXR && !isb;
             int id = 0;
-            if (valid && (k < MAXID || spill)) id = root_id(info);
+            if (valid && (k < MAXID || spill)) id = root_id_early(info);
             if (k0 < MAXID) {
                 const uint32_t bal = __ballot_sync(FULL, valid && isb);
                 if (lane == 0) sBrd[k0 >> 5] = bal;
@@ -287,7 +309,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
         int pf_row = -1;
         for (int r = warp; r < th; r += NWARPS) {
             const uint32_t e = sE[r][lane];
-            const int row_slot = sRowSlot[r], nr = sRowN[r];
+            const int row_slot = sRowBase[r], nr = sRowN[r];
             int32_t *rid = sRid + warp * TW;
             // root ordinals of the row's runs (rid: by run index within the
             // row); the first PF rounds were fetched into registers while the
@@ -325,7 +347,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             {
                 const int rn = r + NWARPS;   // this warp's next row
                 if (rn < th) {
-                    const int ns = sRowSlot[rn];
+                    const int ns = sRowBase[rn];
                     if (sRounds[rn]) {
                         const int cn = __popc(sE[rn][lane]);
 #pragma unroll
@@ -546,15 +568,16 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
                 hash_push(H, d.feat, cap, img, id, v);
             }
         }
-        if (!ok) atomicAnd(&sOk, 0);
-        if (over) atomicOr(&sCap, 1);
+        if (!ok) atomicAnd(&sOk[q], 0);
+        if (over) atomicOr(&sCap[q], 1);
         __syncthreads();
         hash_flush(H, B.desc, false);
         if (threadIdx.x == 0) {
-            if (!sOk) set_status(B, d, ST_ITER);
-            if (sCap) set_status(B, d, ST_CAPACITY);
+            if (!sOk[q]) set_status(B, d, ST_ITER);
+            if (sCap[q]) set_status(B, d, ST_CAPACITY);
+            sOk[q] = 1;   // the slot is next used two tiles on
+            sCap[q] = 0;
         }
-        __syncthreads();
     }
 }
 
