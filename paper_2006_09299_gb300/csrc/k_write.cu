@@ -86,8 +86,63 @@ __device__ __forceinline__ void warp_combine(RunAcc &a, int lane) {
     if (lane < 31 && knext == a.k) a.k = -1;   // not the group's last lane
 }
 
+// Per-tile combining table for the features of border roots, which the
+// cross-tile merge may have joined to the same node: every entry of one tile
+// belongs to the tile's image, so the key is the node id and the sums are
+// tile-relative and fit 32 bits (area <= 2^15, sum of x - x0 < 2^24, sum of
+// y - y0 < 2^20); rows is a mask of the tile rows the contributions cover.
+// It lives in the run buffers once the label rows are written: 28 bytes per
+// entry, 1024 entries for 32-row tiles, 512 for 16-row tiles.
+template <int N> struct TileHash {
+    static constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+    uint32_t *key, *area, *sx, *sy, *xmin, *xmax, *rows;
+    __device__ __forceinline__ explicit TileHash(void *mem) {
+        key = (uint32_t *)mem;
+        area = key + N;
+        sx = area + N;
+        sy = sx + N;
+        xmin = sy + N;
+        xmax = xmin + N;
+        rows = xmax + N;
+    }
+    __device__ __forceinline__ void init(int tid, int nthreads) const {
+        const uint4 e = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY), z = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < N / 4; i += nthreads) {
+            ((uint4 *)key)[i] = e;
+            ((uint4 *)area)[i] = z;
+            ((uint4 *)sx)[i] = z;
+            ((uint4 *)sy)[i] = z;
+            ((uint4 *)xmin)[i] = e;
+            ((uint4 *)xmax)[i] = z;
+            ((uint4 *)rows)[i] = z;
+        }
+    }
+    // false when the probes found no free entry (the caller adds to the
+    // global record directly)
+    __device__ __forceinline__ bool push(uint32_t id, uint32_t a, uint32_t lsx, uint32_t lsy, uint32_t lx0,
+                                         uint32_t lx1, uint32_t rmask) const {
+        constexpr int BITS = N == 1024 ? 10 : 9;
+        static_assert(N == 1024 || N == 512, "table sizes");
+        const uint32_t h = (id * 2654435761u) >> (32 - BITS);
+        for (int probe = 0; probe < 16; ++probe) {
+            const int e = (int)((h + probe) & (N - 1));
+            const uint32_t prev = atomicCAS(key + e, EMPTY, id);
+            if (prev == EMPTY || prev == id) {
+                atomicAdd(area + e, a);
+                atomicAdd(sx + e, lsx);
+                atomicAdd(sy + e, lsy);
+                atomicMin(xmin + e, lx0);
+                atomicMax(xmax + e, lx1);
+                atomicOr(rows + e, rmask);
+                return true;
+            }
+        }
+        return false;
+    }
+};
+
 __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e) {
-    asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e) : "memory");
+    asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e));
 }
 
 template <int TH>
@@ -119,8 +174,9 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
     __shared__ int4 sSt[2];
     __shared__ __align__(8) uint64_t sHBar;
 
-    // the hash table reuses the run buffers once the rows are written
-    const HashTab H = hash_carve(sRid);
+    // the combining table reuses the run buffers once the rows are written
+    const TileHash<(TH == 32 ? 1024 : 512)> H(sRid);
+    static_assert((TH == 32 ? 1024 : 512) * 7 <= NWARPS * TW, "table fits the run buffers");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // thread 0: bulk-copy the header and counts of tile tn into slot `slot`
@@ -447,7 +503,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             if (labels) {
                 int32_t *fgrow = d.fg + (int64_t)(y0 + r) * h.w + x0;
                 int32_t *bgrow = d.bg + (int64_t)(y0 + r) * h.w + x0;
-#pragma unroll 2
+#pragma unroll
                 for (int k8 = 0; k8 < TW / 128; ++k8) {
                     const int x = 128 * k8 + 4 * lane;
                     if (x < tw) {
@@ -521,7 +577,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
 
         // ---- per local root: features (records of multi-run roots; the
         // run itself for a single-run root)
-        hash_init(H);
+        H.init(threadIdx.x, NTHREADS);
         __syncthreads();
         uint32_t fin_next = threadIdx.x < n_roots ? ri[threadIdx.x] : 0u;   // one iteration ahead
         for (int k = threadIdx.x; k < n_roots; k += NTHREADS) {
@@ -532,28 +588,33 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             const bool isb = (info >> 17) & 1u;
             const int id = k < MAXID ? sId[k] : root_id(info);
             if (id >= cap) continue;
-            long long area, sx, sy;
-            int xmin, xmax, ymin = y0 + r, ymax;
+            // tile-relative features first
+            uint32_t la, lsx, lsy, lx0, lx1, rmask;
             if (k < n_multi) {
-                area = (long long)sArea[k];
-                sx = (long long)sSx[k] + area * x0;
-                sy = (long long)sSy[k] + area * y0;
-                xmin = x0 + (int)sX0[k];
-                xmax = x0 + (int)sX1[k];
-                ymax = y0 + 31 - __clz(sRows[k]);
+                la = sArea[k];
+                lsx = sSx[k];
+                lsy = sSy[k];
+                lx0 = sX0[k];
+                lx1 = sX1[k];
+                rmask = sRows[k];
             } else {
                 // the run starting at (r, c) ends before the next run start
                 int l = c >> 5;
                 uint32_t m = sE[r][l] & ~mask_le(c & 31);
                 while (!m && ++l < WPR) m = sE[r][l];
                 const int ce = m ? min(32 * l + __ffs(m) - 1, tw) : tw;
-                area = ce - c;
-                sx = (long long)(x0 + c + x0 + ce - 1) * area / 2;
-                sy = (long long)ymin * area;
-                xmin = x0 + c;
-                xmax = x0 + ce - 1;
-                ymax = ymin;
+                la = (uint32_t)(ce - c);
+                lsx = (uint32_t)((c + ce - 1) * (ce - c) / 2);
+                lsy = (uint32_t)r * la;
+                lx0 = (uint32_t)c;
+                lx1 = (uint32_t)(ce - 1);
+                rmask = 1u << r;
             }
+            if (isb && H.push((uint32_t)id, la, lsx, lsy, lx0, lx1, rmask)) continue;
+            const long long area = la;
+            const long long sx = (long long)lsx + area * x0, sy = (long long)lsy + area * y0;
+            const int xmin = x0 + (int)lx0, xmax = x0 + (int)lx1;
+            const int ymin = y0 + __ffs(rmask) - 1, ymax = y0 + 31 - __clz(rmask);
             if (!isb) {
                 d.feat[0 * cap + id] = area;
                 d.feat[1 * cap + id] = xmin;
@@ -563,15 +624,22 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
                 d.feat[5 * cap + id] = sx;
                 d.feat[6 * cap + id] = sy;
             } else {
-                const FeatAcc v{(unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
-                                xmin, ymin, xmax, ymax};
-                hash_push(H, d.feat, cap, img, id, v);
+                feat_atomic(d.feat, cap, id, (unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
+                            xmin, ymin, xmax, ymax);
             }
         }
         if (!ok) atomicAnd(&sOk[q], 0);
         if (over) atomicOr(&sCap[q], 1);
         __syncthreads();
-        hash_flush(H, B.desc, false);
+        for (int e = threadIdx.x; e < (TH == 32 ? 1024 : 512); e += NTHREADS) {
+            const uint32_t id = H.key[e];
+            if (id == H.EMPTY) continue;
+            const unsigned long long a = H.area[e];
+            const uint32_t rm = H.rows[e];
+            feat_atomic(d.feat, cap, (int)id, a, H.sx[e] + a * (unsigned long long)x0,
+                        H.sy[e] + a * (unsigned long long)y0, x0 + (int)H.xmin[e], y0 + __ffs(rm) - 1,
+                        x0 + (int)H.xmax[e], y0 + 31 - __clz(rm));
+        }
         if (threadIdx.x == 0) {
             if (!sOk[q]) set_status(B, d, ST_ITER);
             if (sCap[q]) set_status(B, d, ST_CAPACITY);
