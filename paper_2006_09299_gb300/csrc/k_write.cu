@@ -141,6 +141,23 @@ template <int N> struct TileHash {
     }
 };
 
+// A contribution to a node record. Apart from the exterior (node 0), a
+// record written with atomics already holds its exact ymin: a border node's
+// record starts at its first pixel's row (node ids pass), a spilled record
+// at its root's row, and no pixel of a component lies above its first
+// pixel. So six atomics instead of seven.
+__device__ __forceinline__ void feat_add(int64_t *base, int64_t cap, int id, unsigned long long area,
+                                         unsigned long long sx, unsigned long long sy, long long xmin, long long ymin,
+                                         long long xmax, long long ymax) {
+    atomicAdd((unsigned long long *)(base + 0 * cap + id), area);
+    atomicMin((long long *)(base + 1 * cap + id), xmin);
+    if (id == 0) atomicMin((long long *)(base + 2 * cap + id), ymin);
+    atomicMax((long long *)(base + 3 * cap + id), xmax);
+    atomicMax((long long *)(base + 4 * cap + id), ymax);
+    atomicAdd((unsigned long long *)(base + 5 * cap + id), sx);
+    atomicAdd((unsigned long long *)(base + 6 * cap + id), sy);
+}
+
 __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e) {
     asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e));
 }
@@ -446,8 +463,8 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
                     } else {
                         const int id = root_id(ri[a.k]);
                         if (id < cap)
-                            feat_atomic(d.feat, cap, id, a.len, a.sx + (unsigned long long)x0 * a.len,
-                                        (unsigned long long)(y0 + r) * a.len, x0 + a.x0, y0 + r, x0 + a.x1, y0 + r);
+                            feat_add(d.feat, cap, id, a.len, a.sx + (unsigned long long)x0 * a.len,
+                                     (unsigned long long)(y0 + r) * a.len, x0 + a.x0, y0 + r, x0 + a.x1, y0 + r);
                     }
                 };
                 // one run into the accumulator of its parity (the caller
@@ -624,8 +641,8 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
                 d.feat[5 * cap + id] = sx;
                 d.feat[6 * cap + id] = sy;
             } else {
-                feat_atomic(d.feat, cap, id, (unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
-                            xmin, ymin, xmax, ymax);
+                feat_add(d.feat, cap, id, (unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
+                         xmin, ymin, xmax, ymax);
             }
         }
         if (!ok) atomicAnd(&sOk[q], 0);
@@ -636,9 +653,8 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             if (id == H.EMPTY) continue;
             const unsigned long long a = H.area[e];
             const uint32_t rm = H.rows[e];
-            feat_atomic(d.feat, cap, (int)id, a, H.sx[e] + a * (unsigned long long)x0,
-                        H.sy[e] + a * (unsigned long long)y0, x0 + (int)H.xmin[e], y0 + __ffs(rm) - 1,
-                        x0 + (int)H.xmax[e], y0 + 31 - __clz(rm));
+            feat_add(d.feat, cap, (int)id, a, H.sx[e] + a * (unsigned long long)x0, H.sy[e] + a * (unsigned long long)y0,
+                     x0 + (int)H.xmin[e], y0 + __ffs(rm) - 1, x0 + (int)H.xmax[e], y0 + 31 - __clz(rm));
         }
         if (threadIdx.x == 0) {
             if (!sOk[q]) set_status(B, d, ST_ITER);
