@@ -272,7 +272,9 @@ void launch_fill(const Batch &B, int64_t T, int32_t target, const LaunchCfg &c, 
     if (ev) cudaEventRecord(ev[0], st);
     k_fill_map<<<grid, 256, 0, st>>>(B, T, target);
     if (ev) cudaEventRecord(ev[1], st);
-    k_fill_merge<<<grid, 256, 0, st>>>(B);
+    // the merge needs 64 registers per thread, so four of its CTAs fit an
+    // SM: one resident wave, one table flush per CTA
+    k_fill_merge<<<4 * c.sms, 256, 0, st>>>(B);
     if (ev) cudaEventRecord(ev[2], st);
 }
 
