@@ -9,7 +9,13 @@ Frames (uint8 host arrays of mixed sizes) arrive one by one. The server
     stream; each stream has its own batched context, so a new tick runs on
     the device while earlier ticks are still in flight;
   - completes a request when its batch's CUDA event has fired: its results
-    are the slot's device tensors, and latency = completion - arrival.
+    are the slot's device tensors, and latency = completion - arrival. They
+    stay valid until the client releases the request: the slot is then
+    reused (or freed when memory is needed for another size class), and the
+    request drops its reference to them;
+  - if a scheduler pass fails (an allocation or a launch raises), every
+    request not yet completed is completed with status "failed", the error
+    is kept in Server.error, and later submissions raise.
 
 The scheduling logic (admission, batching, stream rotation, completion) is
 plain Python over a backend object; GpuBackend drives the CUDA library, and
@@ -73,10 +79,13 @@ class Server:
         self._thread = None
         self._rid = 0
         self.ticks = 0
+        self.error = None
 
     # ------------------------------------------------------------ clients
     def submit(self, frame, t_arrive=None):
         with self.lock:
+            if self.error is not None:
+                raise RuntimeError("the serving scheduler failed: %r" % (self.error,))
             r = Request(self._rid, frame, time.perf_counter() if t_arrive is None else t_arrive)
             self._rid += 1
             self.waiting.append(r)
@@ -187,10 +196,24 @@ class Server:
         self.inflight = still
 
     def release(self, req):
-        """Give a finished request's slot back (its result tensors are reused)."""
+        """Give a finished request's slot back: its result tensors are reused,
+        so the request drops them (an evicted slot's memory is then freed)."""
         with self.lock:
             self._release(req)
+            req.result = None
         self.wake.set()
+
+    def _fail(self, err):
+        """A scheduler pass raised: complete every pending request as failed."""
+        with self.lock:
+            self.error = err
+            pending = list(self.waiting) + list(self.admitted) + [r for _, _, b in self.inflight for r in b]
+            self.waiting.clear()
+            self.admitted.clear()
+            self.inflight = []
+            for r in pending:
+                r.status = "failed"
+                r.done.set()
 
     def step(self):
         """One scheduler pass: completions, admission, launches."""
@@ -209,13 +232,16 @@ class Server:
         sys.setswitchinterval(switch_interval)
 
         def loop():
-            while not self._stop:
-                busy = self.step()
-                if not busy:
-                    self.wake.wait(0.002)
-                    self.wake.clear()
-                else:
-                    time.sleep(poll_s)
+            try:
+                while not self._stop:
+                    busy = self.step()
+                    if not busy:
+                        self.wake.wait(0.002)
+                        self.wake.clear()
+                    else:
+                        time.sleep(poll_s)
+            except Exception as e:   # reported through Server.error and the requests
+                self._fail(e)
         self._thread = threading.Thread(target=loop, daemon=True)
         self._thread.start()
 
@@ -319,14 +345,16 @@ class GpuBackend:
 # ----------------------------------------------------------------- driver
 
 
-def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True):
+def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True, drain_s=30.0):
     """Submit frames (cycled) with Poisson arrivals at rate_hz for duration_s;
-    wait for the admitted work to finish. Returns the completed requests and
-    the queue depth seen at the end of the arrival window."""
+    wait (at most drain_s in all) for the admitted work to finish. Returns the
+    requests and the queue depth seen at the end of the arrival window;
+    raises if the scheduler failed."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     t_next = t0
     reqs = []
+    unreleased = collections.deque()
     i = 0
     while True:
         t_next += rng.exponential(1.0 / rate_hz)
@@ -335,18 +363,26 @@ def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True):
         wait = t_next - time.perf_counter()
         if wait > 0:
             time.sleep(wait)          # releases the interpreter to the scheduler
+        if server.error is not None:
+            raise RuntimeError("the serving scheduler failed") from server.error
         reqs.append(server.submit(frames[i % len(frames)], t_arrive=t_next))
+        unreleased.append(reqs[-1])
         i += 1
-        # hand back the slots of finished requests (their results were consumed)
+        # hand back the slots of finished requests (their results were
+        # consumed), oldest first: requests finish roughly in arrival order
         if release:
-            for r in reqs[max(0, len(reqs) - 64):]:
-                if r.done.is_set() and r.slot is not None:
+            while unreleased and unreleased[0].done.is_set():
+                r = unreleased.popleft()
+                if r.slot is not None:
                     server.release(r)
     depth_end = server.queue_depth()
+    deadline = time.perf_counter() + drain_s
     for r in reqs:
-        r.done.wait(30.0)
-        if release and r.slot is not None:
+        r.done.wait(max(0.0, deadline - time.perf_counter()))
+        if release and r.slot is not None and r.done.is_set():
             server.release(r)
+    if server.error is not None:
+        raise RuntimeError("the serving scheduler failed") from server.error
     return reqs, depth_end
 
 

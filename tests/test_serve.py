@@ -189,3 +189,57 @@ def test_preallocate_respects_budget_and_is_reused():
     r = s.submit(np.zeros((10, 10), np.uint8))
     s.step()
     assert r.slot is not None and be.alloc == allocated   # an idle slot was reused
+
+
+def test_release_drops_the_result_so_evicted_slots_are_freed():
+    be = FakeBackend(delay=0.0)
+    s = Server(be, memory_budget=10**9, max_batch=4, n_streams=1)
+    r = s.submit(np.zeros((2, 2), np.uint8))
+    drain(s)
+    assert r.done.is_set() and r.result == "res%d" % r.rid
+    s.release(r)
+    # the slot's tensors are reused from here on: the request holds none of them
+    assert r.slot is None and r.result is None
+    assert len(s.free_slots[(2, 2)]) == 1
+
+
+class FailingBackend(FakeBackend):
+    """Raises on its n-th launch, as an out-of-memory allocation would."""
+
+    def __init__(self, fail_at, **kw):
+        super().__init__(**kw)
+        self.fail_at = fail_at
+
+    def launch(self, k, batch, T):
+        if len(self.launches) + 1 >= self.fail_at:
+            raise MemoryError("device allocation failed")
+        return super().launch(k, batch, T)
+
+
+def test_a_failed_scheduler_pass_fails_pending_requests_and_the_driver():
+    be = FailingBackend(fail_at=3, delay=0.001)
+    s = Server(be, memory_budget=10**9, max_batch=2, n_streams=2)
+    s.start()
+    t0 = time.perf_counter()
+    try:
+        with pytest.raises(RuntimeError):
+            poisson_run(s, [np.zeros((3, 3), np.uint8)], rate_hz=2000, duration_s=0.3, drain_s=5.0)
+    finally:
+        s.stop()
+    assert time.perf_counter() - t0 < 5.0            # no request is waited on after the failure
+    assert isinstance(s.error, MemoryError)
+    with pytest.raises(RuntimeError):
+        s.submit(np.zeros((3, 3), np.uint8))
+
+
+def test_the_driver_waits_a_bounded_time_for_unfinished_work():
+    be = FakeBackend(delay=10.0)                      # batches that never finish in time
+    s = Server(be, memory_budget=10**9, max_batch=4, n_streams=1)
+    s.start()
+    t0 = time.perf_counter()
+    try:
+        reqs, _ = poisson_run(s, [np.zeros((3, 3), np.uint8)], rate_hz=500, duration_s=0.1, drain_s=0.5)
+    finally:
+        s.stop()
+    assert time.perf_counter() - t0 < 3.0
+    assert any(not r.done.is_set() for r in reqs)
