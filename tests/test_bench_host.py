@@ -1,0 +1,35 @@
+"""Host-side logic of bench.py that decides what the JSON line reports: the
+recorded DRAM traffic is used only while the kernel's code is unchanged."""
+import json
+
+import pytest
+
+import bench
+
+
+def test_source_hash_ignores_comments_and_layout(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2006_09299_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "k.cu").write_text("int f(int a) {\n    return a + 1;   // one more\n}\n")
+    h0 = bench.kernel_source_hash("k.cu")
+    (csrc / "k.cu").write_text("/* block\n comment */ int f(int a) { return a + 1; }  // changed comment\n\n")
+    assert bench.kernel_source_hash("k.cu") == h0
+    (csrc / "k.cu").write_text("int f(int a) {\n    return a + 2;\n}\n")
+    assert bench.kernel_source_hash("k.cu") != h0
+
+
+def test_recorded_traffic_scales_and_goes_stale(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2006_09299_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "k.cu").write_text("int f(int a) { return a; }\n")
+    rec = {"k.cu": {"file": "k.cu", "source_sha256_16": bench.kernel_source_hash("k.cu"),
+                    "dram_bytes_per_pixel": {"sweep4096": 9.5}}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.recorded_traffic("k.cu", "sweep4096", 1000) == pytest.approx(9500.0)
+    assert bench.recorded_traffic("k.cu", "rings8192", 1000) is None      # not captured there
+    (csrc / "k.cu").write_text("int f(int a) { return -a; }\n")
+    assert bench.recorded_traffic("k.cu", "sweep4096", 1000) is None      # code changed since
+
