@@ -20,6 +20,7 @@ same workload and metric, a bounded sample of images per step.
 Prints one JSON line (rank 0).
 """
 import argparse
+import copy
 import hashlib
 import json
 import os
@@ -277,6 +278,22 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if args.workload == "sweep4096" and not args.no_extra:
         extra["batched_vs_plain"] = batched_vs_plain(ccl, dev, stream)
+        # the labels-off form of this workload (tree, features, counts; 1 B/px)
+        offs = [copy.copy(o) for o in outs]
+        for o in offs:
+            o.fg = o.bg = None
+        ms_off = timed_ms(lambda: ctx.analyze(d_imgs, outs=offs), args.steps, args.warmup, stream)
+        ph_off = phase_times(ctx, lambda: ctx.analyze(d_imgs, outs=offs), args.steps)
+        peak, peak_kind = measured_peaks()
+        extra["labels_off"] = {"workload": args.workload, "ms": round(ms_off, 4), "gpx_s": round(px / ms_off / 1e6, 2),
+                               "phase_ms": ph_off,
+                               "roofline": hbm_roofline("whole analysis, labels off", IMAGE_BYTES_PER_PX, px, ms_off,
+                                                        peak, peak_kind, args.workload),
+                               "outputs": "tree, features, counts (Euler number = n_fg - n_bg + 1); no label images"}
+        from paper_2006_09299_gb300 import inputs
+        extra["rings8192"] = single_image_record(ccl, dev, stream, inputs.rings(), 8192, args.steps, args.warmup,
+                                                 "rings8192", cpu=world == 1 and not args.no_cpu_baseline)
+        extra["latency_512"] = latency_512(ccl, dev, stream)
 
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gpixel/s", "n_gpus": world,
@@ -354,7 +371,7 @@ def run_e2e(args, ctx, imgs, outs, dev, stream, px):
     out_done = [[ev() for _ in range(N_OUT)] for _ in range(2)]
     for e in comp_done + out_done[0] + out_done[1]:
         e.record(s_comp)
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, args.steps)
     bytes_in = sum(h.numel() for h in h_imgs)
     d2h = [0]
 
@@ -412,6 +429,157 @@ def run_e2e(args, ctx, imgs, outs, dev, stream, px):
             "d2h_bytes_per_step": d2h[0], "steps": steps,
             "includes": "H2D images, analyse + fill, D2H counts, fg/bg labels, tree and features; "
                         "copy-in, analysis and copy-out (4 streams) overlapped, two device buffer sets"}
+
+
+def timed_ms(step, steps, warmup, stream):
+    """Average device time of one step (CUDA events on the launching stream,
+    after warm-up, synchronised on both sides)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def phase_times(ctx, step, steps):
+    """Per-phase device time of `steps` calls of step (events around every
+    launch of the library), ms per call."""
+    import torch
+    ctx.enable_phase_timing(2 * steps)
+    torch.cuda.synchronize()
+    for _ in range(steps):
+        step()
+    phases = ctx.read_phase_timing()
+    ctx.enable_phase_timing(0)
+    return {k: round(v[0] / v[1], 4) for k, v in phases.items() if v[1]}
+
+
+def hbm_roofline(kernel, bytes_per_px, px, ms, peak, peak_kind, workload, kernel_file=None):
+    alg = bytes_per_px * px
+    achieved = alg / (ms * 1e-3) / 1e9
+    r = {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+         "frac": round(achieved / peak, 4), "algorithmic_bytes": alg, "algorithmic_bytes_per_pixel": bytes_per_px,
+         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, of measured)", "avg_launch_ms": round(ms, 4)}
+    if kernel_file:
+        r["traffic"] = recorded_traffic(kernel_file, workload, px)
+    return r
+
+
+def single_image_record(ccl, dev, stream, img, w, steps, warmup, name, cpu=True):
+    """One image through the single-image API (ccl_create / ccl_analyze /
+    ccl_fill_holes): the analysis alone (fg + bg labels, tree, features),
+    the analysis with hole filling (area threshold 64), and the analysis with
+    the label images off; per-phase times, rooflines and the oracle on one
+    host core."""
+    import torch
+    from paper_2006_09299_gb300 import autotune
+    h = img.shape[0]
+    px = w * h
+    peak, peak_kind = measured_peaks()
+    d_img = torch.from_numpy(np.ascontiguousarray(img)).to(dev)
+    ctx = ccl.Context(w, h, img.shape[1])
+    out = ctx.new_outputs(True, dev)
+    out.alloc_fill()
+    off = ctx.new_outputs(False, dev)
+
+    def analysis():
+        ctx.analyze(d_img, out=out)
+
+    def analysis_fill():
+        ctx.analyze(d_img, out=out)
+        ctx.fill_holes(FILL_T, out=out)
+
+    def labels_off():
+        ctx.analyze(d_img, out=off)
+
+    rows, tune_ms = autotune.tune(ctx, analysis, autotune.size_class([(w, h)]),
+                                  cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=3, warmup=2)
+    launches0 = ctx.launch_count()
+    ms_a = timed_ms(analysis, steps, warmup, stream)
+    ms_af = timed_ms(analysis_fill, steps, warmup, stream)
+    ms_off = timed_ms(labels_off, steps, warmup, stream)
+    launches = (ctx.launch_count() - launches0) // (steps + warmup)
+    if out.status() or off.status():
+        raise RuntimeError("device status set in the %s record" % name)
+    ph = phase_times(ctx, analysis_fill, steps)
+    ph_off = phase_times(ctx, labels_off, steps)
+    n_nodes = out.n
+    rec = {
+        "workload": name, "pixels": px, "nodes": n_nodes, "tile": {"rows": rows, "cols": 1024,
+                                                                  "tuning_ms": {str(k): round(v, 4) for k, v in tune_ms.items()}},
+        "api": "ccl_create + ccl_analyze (+ ccl_fill_holes), one image",
+        "steps": steps, "warmup": warmup,
+        "analysis_ms": round(ms_a, 4), "analysis_gpx_s": round(px / ms_a / 1e6, 2),
+        "analysis_fill_ms": round(ms_af, 4), "analysis_fill_gpx_s": round(px / ms_af / 1e6, 2),
+        "phase_ms": ph,
+        "path_roofline": hbm_roofline("whole analysis (all kernels)", PATH_BYTES_PER_PX, px, ms_a, peak, peak_kind, name),
+        "roofline_kernels": [hbm_roofline("k_label", IMAGE_BYTES_PER_PX, px, ph["label"], peak, peak_kind, name, "k_label.cu"),
+                             hbm_roofline("k_write", LABEL_BYTES_PER_PX, px, ph["write"], peak, peak_kind, name, "k_write.cu")],
+        "labels_off": {"ms": round(ms_off, 4), "gpx_s": round(px / ms_off / 1e6, 2), "phase_ms": ph_off,
+                       "roofline": hbm_roofline("whole analysis, labels off", IMAGE_BYTES_PER_PX, px, ms_off, peak,
+                                                peak_kind, name),
+                       "outputs": "tree, features, counts (Euler number = n_fg - n_bg + 1); no label images"},
+        "launches_per_analysis_fill": launches // 3 if launches else None,
+    }
+    if cpu:
+        from oracle import reference as orc
+        orc.build()
+        t = time.perf_counter()
+        r = orc.analyze(img, w=w)
+        orc.fill(r, FILL_T)
+        dt = time.perf_counter() - t
+        rec["cpu_baseline"] = {"value": round(px / dt / 1e9, 5), "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
+                               "sample": "the whole image once: analysis + fill 64, C flood-fill oracle, 1 host thread"}
+    ctx.close()
+    return rec
+
+
+def latency_512(ccl, dev, stream, calls=200, warmup=20):
+    """512 x 512 Bernoulli(0.5) image, seed 1: median latency of single
+    ccl_analyze calls (each timed alone with CUDA events, synchronised), and
+    of ccl_analyze_static on the same image."""
+    import torch
+    from paper_2006_09299_gb300 import inputs
+    img = inputs.bernoulli(512, 512, 0.5, 1)
+    d_img = torch.from_numpy(img).to(dev)
+    ctx = ccl.Context(512, 512, 512)
+    out = ctx.new_outputs(True, dev)
+    sout = ccl.Analysis(512, 512, ccl.node_capacity(512, 512), True, dev)
+
+    def med(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(calls):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        return statistics.median(ts), min(ts)
+
+    us, us_min = med(lambda: ctx.analyze(d_img, out=out))
+    sus, sus_min = med(lambda: ccl.analyze_static(d_img, 512, sout, stream=stream))
+    if out.status() or sout.status():
+        raise RuntimeError("device status set in the 512x512 record")
+    ctx.close()
+    px = 512 * 512
+    return {"workload": "512x512 uint8, i.i.d. Bernoulli(0.5), seed 1; fg 8-conn, bg 4-conn",
+            "calls": calls, "warmup": warmup,
+            "ccl_analyze_median_us": round(us, 2), "ccl_analyze_min_us": round(us_min, 2),
+            "ccl_analyze_gpx_s": round(px / us / 1e3, 3),
+            "ccl_analyze_static_median_us": round(sus, 2), "ccl_analyze_static_gpx_s": round(px / sus / 1e3, 3),
+            "note": "each call timed alone (launch latency included); the image and its outputs stay in L2"}
 
 
 def batched_vs_plain(ccl, dev, stream, reps=5):
@@ -541,26 +709,38 @@ def cpu_baseline(imgs, budget_s=12.0, all_cores=False):
 
 
 def run_reference(args, rank, world):
+    """The oracle (C flood fill, one host thread) on a bounded sample of the
+    workload: every step analyses and fills a fixed number of the workload's
+    images (rotating through them), and ms_per_step is the time of exactly
+    those images, so that steps x ms_per_step is the timed region."""
     imgs = workload_images(args.workload)
-    px = sum(p.shape[0] * w for p, w in imgs)
-    # bounded sample per step: rotate through the images, ~budget per step
     per_step = max(1, min(len(imgs), 2))
-    rates = []
+    from oracle import reference as orc
+    orc.build()
+    times, pxs = [], []
     for s in range(args.warmup + args.steps):
         sample = [imgs[(s * per_step + k) % len(imgs)] for k in range(per_step)]
-        rate, n, dpx, t = oracle_rate(sample, 1e9)
+        t = time.perf_counter()
+        for p, w in sample:
+            r = orc.analyze(p, w=w)
+            orc.fill(r, FILL_T)
+        dt = time.perf_counter() - t
         if s >= args.warmup:
-            rates.append((dpx, t))
-    dpx = sum(a for a, b in rates)
-    t = sum(b for a, b in rates)
-    value = dpx / t / 1e9
-    ms = px / (value * 1e9) * 1e3
+            times.append(dt)
+            pxs.append(sum(p.shape[0] * w for p, w in sample))
+    t = sum(times)
+    value = sum(pxs) / t / 1e9
+    cfg = workload_desc(args.workload, imgs)
+    full_px = cfg["pixels_per_step"]
+    cfg = dict(cfg, pixels_per_step=int(statistics.mean(pxs)), images_per_step=per_step,
+               sample="%d of the workload's %d images per step (rotating), analysis + fill %d; the workload's full "
+                      "step is %d pixels" % (per_step, len(imgs), FILL_T, full_px))
     return {
         "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gpixel/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / len(times), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded generators shaped like the paper's workloads)",
-        "config": workload_desc(args.workload, imgs),
+        "config": cfg,
         "cpu_baseline": {"value": round(value, 5), "unit": "Gpixel/s", "cores": 1, "kind": "oracle",
                          "sample": "%d images per step of the workload, C flood-fill oracle, 1 host thread" % per_step},
         "e2e": {"value": round(value, 5), "unit": "Gpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -605,7 +785,7 @@ def run_serve(args):
         st = latency_stats(reqs)
         done = [r for r in reqs if r.t_done is not None]
         span = (max(r.t_done for r in done) - min(r.t_arrive for r in done)) if done else 1.0
-        px = sum(r.frame.size for r in done)
+        px = sum(r.pixels for r in done)
         row = dict(rate_hz=rate, frames=len(reqs), queue_at_end=depth, gpx_s=round(px / span / 1e9, 3),
                    ticks=ticks, **st)
         row["sustained"] = depth <= 2 * args.serve_batch and len(done) == len(reqs)

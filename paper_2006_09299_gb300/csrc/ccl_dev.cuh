@@ -72,20 +72,9 @@ struct ImgDesc {
     int32_t pad_;
 };
 
-// Device scratch, carved out of one allocation by the host.
-// Layout of a tile's run_root region, row after row. A dense row of a
-// full-width tile (more than RR_ROUND_MIN runs) is stored round by round: the
-// j-th run starting in word l is at row_slot + 32 j + l, and the row takes 32
-// x (the most runs starting in one word) entries, so that a warp writes 32
-// consecutive entries per round. Other rows are stored in raster order (the
-// row takes as many entries as it has runs).
-constexpr int RR_ROUND_MIN = 256;
-
-__device__ __forceinline__ bool rr_rounds(int tw, int runs_in_row) { return tw == TW && runs_in_row > RR_ROUND_MIN; }
-
-__device__ __forceinline__ int rr_slot(bool rounds, int row_slot, int pre_in_row, int lane, int j) {
-    return rounds ? row_slot + 32 * j + lane : row_slot + pre_in_row + j;
-}
+// Device scratch, carved out of one allocation by the host. A tile's
+// run_root region holds one entry per run of the tile, in raster order of the
+// runs (the run ordinal).
 
 // Geometry of one tile, written once per analysis by the prologue and
 // fetched by the tile kernels with a bulk copy ahead of use.
@@ -100,7 +89,7 @@ struct __align__(16) TileHdr {
 struct Scratch {
     uint32_t *fgbits;          // [segs*32] foreground bit plane, rows of TX*32 words
     uint32_t *nodebits;        // [segs*32] 1 at the first pixel of every node
-    uint16_t *run_root;        // [pixels] root ordinal of every run, per tile (layout: rr_slot)
+    uint16_t *run_root;        // [pixels] root ordinal of every run, per tile, by run ordinal
     uint32_t *rootinfo;        // [pixels] per local root, see k_label.cu
     int4 *tstat;               // [tiles] {runs, roots, border roots, image}
     int4 *tsrc;                // [tiles] {first image byte (lo, hi), pitch, rows | copy bytes << 8}

@@ -183,9 +183,8 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
     uint32_t(*sNB)[WPR] = sE + TH;
     uint16_t(*sRunPre)[WPR] = (uint16_t(*)[WPR])(sNB + TH);
     uint16_t(*sNBPre)[WPR] = sRunPre + TH;
-    __shared__ int sRowN[TH], sRowSeg[TH], sRowSlot[TH];   // runs, first node, run-root slots
-    __shared__ int sRowBase[TH];                           // first run-root slot
-    __shared__ bool sRounds[TH];
+    __shared__ int sRowN[TH], sRowSeg[TH];                 // runs, first node
+    __shared__ int sRowBase[TH];                           // run ordinal of the row's first run
     __shared__ int sT[2], sOk[2], sCap[2], sAbort;
     __shared__ TileHdr sHdr[2];
     __shared__ int4 sSt[2];
@@ -297,24 +296,17 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             sNB[r][lane] = nb;
             int tot;
             sRunPre[r][lane] = (uint16_t)warp_excl_sum(__popc(e), &tot);
-            const bool rounds = rr_rounds(tw, tot);
-            const int most = (int)__reduce_max_sync(FULL, (unsigned)__popc(e));
-            const int slots = rounds ? 32 * most : tot;
-            if (lane == 0) {
-                sRowN[r] = tot;
-                sRowSlot[r] = slots;
-                sRounds[r] = rounds;
-            }
+            if (lane == 0) sRowN[r] = tot;
             int ntot;
             sNBPre[r][lane] = (uint16_t)warp_excl_sum(__popc(nb), &ntot);
             if (lane == 0) sRowSeg[r] = r < th ? segw[i] - seg_first : 0;
         }
         __syncthreads();
         {
-            // every warp scans the slot counts itself and keeps the prefixes
+            // every warp scans the run counts itself and keeps the prefixes
             // of its own rows (saves a barrier)
             int tot;
-            const int es = warp_excl_sum(lane < TH ? sRowSlot[lane] : 0, &tot);
+            const int es = warp_excl_sum(lane < TH ? sRowN[lane] : 0, &tot);
             if (lane < TH && lane % NWARPS == warp) sRowBase[lane] = es;
             __syncwarp();
         }
@@ -387,51 +379,28 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             // root ordinals of the row's runs (rid: by run index within the
             // row); the first PF rounds were fetched into registers while the
             // warp worked on its previous row
-            if (sRounds[r]) {
-                // round j of lane l holds the j-th run starting in word l
-                const int pre = sRunPre[r][lane], cnt = __popc(e);
 #pragma unroll
-                for (int j = 0; j < PF; ++j)
-                    if (j < cnt) rid[swz(pre + j)] = pf_row == r ? pf[j] : (int)rr[row_slot + 32 * j + lane];
-                // the rest in groups of 8 loads in flight
-                for (int j0 = PF; j0 < cnt; j0 += 8) {
-                    int v[8];
+            for (int j = 0; j < PF; ++j) {
+                const int i = lane + 32 * j;
+                if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[row_slot + i];
+            }
+            // the rest in groups of 8 loads in flight
+            for (int i0 = lane + 32 * PF; i0 < nr; i0 += 8 * 32) {
+                int v[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = j0 + u < cnt ? (int)rr[row_slot + 32 * (j0 + u) + lane] : 0;
+                for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < nr ? (int)rr[row_slot + i0 + 32 * u] : 0;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (j0 + u < cnt) rid[swz(pre + j0 + u)] = v[u];
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < PF; ++j) {
-                    const int i = lane + 32 * j;
-                    if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[row_slot + i];
-                }
-                for (int i0 = lane + 32 * PF; i0 < nr; i0 += 8 * 32) {
-                    int v[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < nr ? (int)rr[row_slot + i0 + 32 * u] : 0;
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        if (i0 + 32 * u < nr) rid[swz(i0 + 32 * u)] = v[u];
-                }
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + 32 * u < nr) rid[swz(i0 + 32 * u)] = v[u];
             }
             {
                 const int rn = r + NWARPS;   // this warp's next row
                 if (rn < th) {
-                    const int ns = sRowBase[rn];
-                    if (sRounds[rn]) {
-                        const int cn = __popc(sE[rn][lane]);
+                    const int nb = sRowBase[rn], nn = sRowN[rn];
 #pragma unroll
-                        for (int j = 0; j < PF; ++j) pf[j] = j < cn ? (int)rr[ns + 32 * j + lane] : 0;
-                    } else {
-                        const int nb = ns, nn = sRowN[rn];
-#pragma unroll
-                        for (int j = 0; j < PF; ++j) {
-                            const int i = lane + 32 * j;
-                            pf[j] = i < nn ? (int)rr[nb + i] : 0;
-                        }
+                    for (int j = 0; j < PF; ++j) {
+                        const int i = lane + 32 * j;
+                        pf[j] = i < nn ? (int)rr[nb + i] : 0;
                     }
                     pf_row = rn;
                 }

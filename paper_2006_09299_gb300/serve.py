@@ -30,12 +30,13 @@ import numpy as np
 
 
 class Request:
-    __slots__ = ("rid", "frame", "t_arrive", "t_admit", "t_launch", "t_done", "slot", "done", "cancelled",
-                 "result", "status")
+    __slots__ = ("rid", "frame", "pixels", "t_arrive", "t_admit", "t_launch", "t_done", "slot", "done",
+                 "cancelled", "result", "status")
 
     def __init__(self, rid, frame, t_arrive):
         self.rid = rid
-        self.frame = frame
+        self.frame = frame              # dropped once the frame is staged into its slot
+        self.pixels = int(frame.size)
         self.t_arrive = t_arrive
         self.t_admit = self.t_launch = self.t_done = None
         self.slot = None
@@ -72,7 +73,7 @@ class Server:
         self.inflight = []                                 # (stream, handle, [Request])
         self.stream_busy = [False] * self.n_streams
         self.next_stream = 0
-        self.completed = []
+        self.launch_failed = []                            # requests of a launch that raised
         self.lock = threading.Lock()
         self.wake = threading.Event()
         self._stop = False
@@ -172,7 +173,15 @@ class Server:
             now = time.perf_counter()
             for r in batch:
                 r.t_launch = now
-            handle = self.backend.launch(k, batch, self.fill_threshold)
+            try:
+                handle = self.backend.launch(k, batch, self.fill_threshold)
+            except Exception:
+                # copies of this batch may already be queued on the device:
+                # its requests are failed with the in-flight ones
+                self.launch_failed.extend(batch)
+                raise
+            for r in batch:
+                r.frame = None      # staged: the server keeps no host frame alive
             self.stream_busy[k] = True
             self.inflight.append((k, handle, batch))
             self.next_stream = (k + 1) % self.n_streams
@@ -187,7 +196,6 @@ class Server:
                 for r, res in zip(batch, results):
                     r.result, r.status = res
                     r.t_done = now
-                    self.completed.append(r)
                     r.done.set()
                 self.stream_busy[k] = False
                 self.backend.retire(handle)
@@ -204,10 +212,19 @@ class Server:
         self.wake.set()
 
     def _fail(self, err):
-        """A scheduler pass raised: complete every pending request as failed."""
+        """A scheduler pass raised: complete every pending request as failed.
+        Requests whose batch may still run on the device lose their slot
+        outright (it is never handed back to the pool, since kernels may
+        still write to it); waiting and admitted requests give theirs back."""
         with self.lock:
             self.error = err
-            pending = list(self.waiting) + list(self.admitted) + [r for _, _, b in self.inflight for r in b]
+            launched = [r for _, _, b in self.inflight for r in b] + self.launch_failed
+            self.launch_failed = []
+            for r in launched:
+                r.slot = None
+            pending = list(self.waiting) + list(self.admitted) + launched
+            for r in self.admitted:
+                self._release(r)
             self.waiting.clear()
             self.admitted.clear()
             self.inflight = []

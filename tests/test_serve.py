@@ -203,6 +203,51 @@ def test_release_drops_the_result_so_evicted_slots_are_freed():
     assert len(s.free_slots[(2, 2)]) == 1
 
 
+def test_the_server_keeps_no_host_frame_alive():
+    import gc
+    import weakref
+    be = FakeBackend(delay=0.0)
+    s = Server(be, memory_budget=10**9, max_batch=4, n_streams=2)
+    refs, reqs = [], []
+    for k in range(64):
+        f = np.full((8, 8 + k % 3), k, np.uint8)   # a fresh host array per request
+        refs.append(weakref.ref(f))
+        reqs.append(s.submit(f))
+        del f
+        s.step()
+    drain(s)
+    for r in reqs:
+        assert r.done.is_set() and r.pixels == 8 * r.slot.key[1]
+        s.release(r)
+    gc.collect()
+    assert all(ref() is None for ref in refs)        # every frame was freed
+
+
+class SlowFailingBackend(FakeBackend):
+    """Launches two batches that stay on the device, then fails."""
+
+    def launch(self, k, batch, T):
+        if len(self.launches) >= 2:
+            raise MemoryError("device allocation failed")
+        return super().launch(k, batch, T)
+
+
+def test_a_failure_never_returns_slots_of_batches_still_on_the_device():
+    be = SlowFailingBackend(delay=10.0)
+    s = Server(be, memory_budget=10**9, max_batch=1, n_streams=3)
+    reqs = [s.submit(np.zeros((2, 2), np.uint8)) for _ in range(4)]
+    with pytest.raises(MemoryError):
+        s.step()
+    s._fail(MemoryError("device allocation failed"))
+    assert len(be.launches) == 2 and sum(r.t_launch is not None for r in reqs) == 3
+    for r in reqs:
+        assert r.done.is_set() and r.status == "failed"
+        s.release(r)
+    # the slots of the two running batches and of the launch that raised
+    # (its copies may be queued) are not in the pool; the admitted one is
+    assert len(s.free_slots[(2, 2)]) == be.alloc - 3
+
+
 class FailingBackend(FakeBackend):
     """Raises on its n-th launch, as an out-of-memory allocation would."""
 
