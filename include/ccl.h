@@ -286,7 +286,7 @@ ccl_status ccl_get_launch_count(ccl_ctx *ctx, int64_t *launches);
  * array keeps the last call's tables otherwise. */
 #define CCL_STATIC_MAX_PIXELS (1 << 20)
 #define CCL_STATIC_MAX_SIDE 4096
-#define CCL_STATIC_SCRATCH_BYTES (10 << 20)
+#define CCL_STATIC_SCRATCH_BYTES (12 << 20)
 ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_t h, int32_t pitch,
                               int32_t *d_fg_labels, int32_t *d_bg_labels, int32_t *d_tree_parent,
                               int64_t *d_features, int64_t capacity, int32_t *d_counts,

@@ -135,7 +135,7 @@ static size_t carve(const Limits &L, Scratch *s, ImgDesc **desc, char *base) {
     const int64_t words = L.segs * WPR;
     s->fgbits = (uint32_t *)take(words * 4);
     s->nodebits = (uint32_t *)take(words * 4);
-    s->run_root = (uint16_t *)take(L.pixels * 2);
+    s->run_root = (uint32_t *)take(L.pixels * 4);
     s->rootinfo = (uint32_t *)take(L.pixels * 4);
     s->tstat = (int4 *)take(L.tiles * 16);
     s->tsrc = (int4 *)take(L.tiles * 16);

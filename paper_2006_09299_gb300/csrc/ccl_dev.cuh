@@ -73,8 +73,9 @@ struct ImgDesc {
 };
 
 // Device scratch, carved out of one allocation by the host. A tile's
-// run_root region holds one entry per run of the tile, in raster order of the
-// runs (the run ordinal).
+// run_root region holds one record per run of the tile, in raster order of
+// the runs (the run ordinal): root ordinal << 16 | first pixel (row * 1024 +
+// column) << 1 | colour.
 
 // Geometry of one tile, written once per analysis by the prologue and
 // fetched by the tile kernels with a bulk copy ahead of use.
@@ -89,7 +90,7 @@ struct __align__(16) TileHdr {
 struct Scratch {
     uint32_t *fgbits;          // [segs*32] foreground bit plane, rows of TX*32 words
     uint32_t *nodebits;        // [segs*32] 1 at the first pixel of every node
-    uint16_t *run_root;        // [pixels] root ordinal of every run, per tile, by run ordinal
+    uint32_t *run_root;        // [pixels] per run: root ordinal << 16 | first pixel << 1 | colour
     uint32_t *rootinfo;        // [pixels] per local root, see k_label.cu
     int4 *tstat;               // [tiles] {runs, roots, border roots, image}
     int4 *tsrc;                // [tiles] {first image byte (lo, hi), pitch, rows | copy bytes << 8}

@@ -119,7 +119,7 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     take(sizeof(ImgDesc));
     s.fgbits = (uint32_t *)take(segs * WPR * 4);
     s.nodebits = (uint32_t *)take(segs * WPR * 4);
-    s.run_root = (uint16_t *)take(px * 2);
+    s.run_root = (uint32_t *)take(px * 4);
     s.rootinfo = (uint32_t *)take(px * 4);
     s.tstat = (int4 *)take(tiles * 16);
     s.tsrc = (int4 *)take(tiles * 16);

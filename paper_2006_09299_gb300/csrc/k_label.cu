@@ -21,8 +21,8 @@
 //   - each union is a union by minimum run ordinal in a shared-memory parent
 //     table, so the root of a tile-local component is its raster-first run,
 //     as the paper's root is its smallest (top-most) label.
-// Results kept for the later phases: every run's root ordinal, one record
-// per local root, the roots of the tile's edge cells (for the cross-tile
+// Results kept for the later phases: every run's root ordinal (with its
+// first pixel and colour), one record per local root, the roots of the tile's edge cells (for the cross-tile
 // merge) and the first-pixel bits of components that stay inside the tile.
 #include "ccl_dev.cuh"
 
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
         const int n_multi = (int)(cnt_tot & 0xFFFFu), n_single = (int)(cnt_tot >> 16);
 
         // ---- per root: record, border slot, ordinal into par[root]
-        uint16_t *rr = B.s.run_root + h.px;
+        uint32_t *rr = B.s.run_root + h.px;
         uint32_t *ri = B.s.rootinfo + h.px;
         const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
         int nfg = 0;
@@ -435,12 +435,12 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
         }
         __syncthreads();
 
-        // ---- per run: root ordinal; per edge cell: border ordinal of its
-        // root; first pixels of the internal nodes
+        // ---- per run: root ordinal and the run's list entry; per edge cell:
+        // border ordinal of its root; first pixels of the internal nodes
         for (int i = tid; i < n; i += NT) {
             uint32_t v = ld_par(par, (uint32_t)i);
             if (!(v & PAR_TAG)) v = ld_par(par, v);
-            rr[i] = (uint16_t)(v & PAR_ORD);
+            rr[i] = ((v & PAR_ORD) << 16) | list[i];
         }
         // (cell i of the loop is also its offset: top, bottom, left, right)
         uint16_t *eg = B.s.edges + h.b;

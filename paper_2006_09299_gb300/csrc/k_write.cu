@@ -3,12 +3,18 @@
 // This is the paper's relabelling (Algorithm 4: every run's pixels receive
 // the final label of the run) fused with the feature merge and the
 // adjacency-to-root step of Algorithm 3:
-//   - each run's root ordinal (from phase 1) gives the run's node id;
+//   - each run's record from phase 1 (its root ordinal, first pixel and
+//     colour) gives the run's node id, through a per-tile table of the
+//     roots' node ids;
 //   - features (ComputeFeatures of Algorithm 2: S, Sx, Sy and the box) are
-//     accumulated per local root in shared memory, run by run; components
-//     that stay inside the tile are then written with plain stores, and
-//     border components are merged into their node with atomics, first
-//     combined per CTA in a small hash table;
+//     accumulated per local root in shared memory, one thread per run; the
+//     runs of one root on one row that sit two runs apart (a component
+//     crossing the row many times) are summed first with a warp scan, so
+//     such a component costs one shared update per warp and row; components
+//     that stay inside the tile are then written with plain
+//     stores, and border components are merged into their node with atomics,
+//     first combined per tile in a small hash table; a root with a single
+//     run in the tile takes its features from that run;
 //   - the tree parent of a node whose first pixel lies in this tile is the
 //     node of the pixel directly above that first pixel (the initial
 //     adjacency of Algorithm 2, kept for the root by Algorithm 3);
@@ -18,72 +24,32 @@
 
 namespace ccl {
 
-
-// Root ordinals of a tile put the roots of components with several runs
-// first, then the single-run roots. Multi-run roots below MAXR accumulate
-// their features in on-chip records (more spill to global atomics); a
-// single-run root's features are those of its run, read back from the bit
-// planes in the feature pass. Node ids of the first MAXID roots are kept on
-// chip. Launch shape per tile height: several CTAs per SM (16 warps in all),
-// so that while one waits on its tile's global reads the others stream label
-// rows; 16-row tiles have half the pixels and half the records.
+// Launch shape per tile height: NT threads, each holding two 32-pixel words
+// of the tile (a warp holds rows w and w + NT / 32), several CTAs per SM so
+// that one streams its label rows while another computes. Root ordinals of a
+// tile put the roots of components with several runs first, then the
+// single-run roots. Multi-run roots below MAXR accumulate their features in
+// on-chip records (more spill to global atomics); node ids of the first
+// MAXID roots are kept on chip (the rest are computed when needed);
+// 2^HASH_BITS entries combine the feature contributions of border roots.
 template <int TH> struct WriteCfg;
-template <> struct WriteCfg<32> { static constexpr int MAXR = 2048, MAXID = 3584, THREADS = 256, CTAS = 2; };
-template <> struct WriteCfg<16> { static constexpr int MAXR = 1024, MAXID = 1792, THREADS = 128, CTAS = 4; };
-
-// Per record: S, Sx, Sy, xmin, xmax and the row mask, all updated with
-// native 32-bit shared reductions (a packed 64-bit sum was slower).
-constexpr int REC_BYTES = 6 * 4;
+template <> struct WriteCfg<32> {
+    static constexpr int NT = 512, MAXR = 2048, MAXID = 8192, HASH_BITS = 9, CTAS = 2;
+};
+template <> struct WriteCfg<16> {
+    static constexpr int NT = 256, MAXR = 1024, MAXID = 3072, HASH_BITS = 8, CTAS = 4;
+};
 
 template <int TH>
 constexpr size_t write_smem() {
-    constexpr int MAXR = WriteCfg<TH>::MAXR, MAXID = WriteCfg<TH>::MAXID;
-    return (size_t)MAXR * REC_BYTES + (size_t)MAXID * 4 + MAXID / 8 + (size_t)(WriteCfg<TH>::THREADS / 32) * TW * 4 +
-           3 * TH * WPR * 4 + 2 * TH * WPR * 2;
-}
-
-// Features of consecutive runs of one root on one row (tile-local x).
-struct RunAcc {
-    int k = -1;
-    uint32_t len = 0, sx = 0;
-    int x0 = 0, x1 = 0;
-    __device__ __forceinline__ void start(int kk, int xs, int xe) {
-        k = kk;
-        len = (uint32_t)(xe - xs);
-        sx = (uint32_t)((xs + xe - 1) * (xe - xs) / 2);
-        x0 = xs;
-        x1 = xe - 1;
-    }
-    __device__ __forceinline__ void add(int xs, int xe) {
-        len += (uint32_t)(xe - xs);
-        sx += (uint32_t)((xs + xe - 1) * (xe - xs) / 2);
-        x1 = xe - 1;
-    }
-};
-
-// Segmented inclusive scan over lanes (lane order = x order) of run
-// accumulators with equal roots; afterwards only the last lane of each group
-// of consecutive lanes with the same root keeps it (the others get k = -1).
-__device__ __forceinline__ void warp_combine(RunAcc &a, int lane) {
-    const int kprev = __shfl_up_sync(FULL, a.k, 1);
-    // nothing to combine unless two consecutive lanes hold the same root
-    if (!__any_sync(FULL, lane > 0 && a.k >= 0 && kprev == a.k)) return;
-    const bool head = lane == 0 || kprev != a.k;
-    int seg = head ? lane : 0;               // lane of this group's first member
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) seg = max(seg, __shfl_up_sync(FULL, seg, d));
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t len = __shfl_up_sync(FULL, a.len, d), sx = __shfl_up_sync(FULL, a.sx, d);
-        const int x0 = __shfl_up_sync(FULL, a.x0, d);
-        if (lane - d >= seg) {
-            a.len += len;
-            a.sx += sx;
-            a.x0 = min(a.x0, x0);
-        }
-    }
-    const int knext = __shfl_down_sync(FULL, a.k, 1);
-    if (lane < 31 && knext == a.k) a.k = -1;   // not the group's last lane
+    using C = WriteCfg<TH>;
+    constexpr size_t NWD = (size_t)TH * WPR;
+    return (size_t)C::MAXR * 6 * 4                // records
+           + (size_t)C::MAXID * 4                 // node id per root
+           + 3 * NWD * 4                          // colour, run-start and node-bit planes
+           + (size_t)7 * 4 * (1 << C::HASH_BITS)  // border combining table
+           + (NWD + 8) * 2                        // first run ordinal of each word
+           + NWD * 2;                             // node bits before each word in its row
 }
 
 // Per-tile combining table for the features of border roots, which the
@@ -91,13 +57,12 @@ __device__ __forceinline__ void warp_combine(RunAcc &a, int lane) {
 // belongs to the tile's image, so the key is the node id and the sums are
 // tile-relative and fit 32 bits (area <= 2^15, sum of x - x0 < 2^24, sum of
 // y - y0 < 2^20); rows is a mask of the tile rows the contributions cover.
-// It lives in the run buffers once the label rows are written: 28 bytes per
-// entry, 1024 entries for 32-row tiles, 512 for 16-row tiles.
-template <int N> struct TileHash {
+template <int BITS> struct TileHash {
+    static constexpr int N = 1 << BITS;
     static constexpr uint32_t EMPTY = 0xFFFFFFFFu;
     uint32_t *key, *area, *sx, *sy, *xmin, *xmax, *rows;
-    __device__ __forceinline__ explicit TileHash(void *mem) {
-        key = (uint32_t *)mem;
+    __device__ __forceinline__ explicit TileHash(uint32_t *mem) {
+        key = mem;
         area = key + N;
         sx = area + N;
         sy = sx + N;
@@ -105,24 +70,19 @@ template <int N> struct TileHash {
         xmax = xmin + N;
         rows = xmax + N;
     }
-    __device__ __forceinline__ void init(int tid, int nthreads) const {
-        const uint4 e = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY), z = make_uint4(0u, 0u, 0u, 0u);
-        for (int i = tid; i < N / 4; i += nthreads) {
-            ((uint4 *)key)[i] = e;
-            ((uint4 *)area)[i] = z;
-            ((uint4 *)sx)[i] = z;
-            ((uint4 *)sy)[i] = z;
-            ((uint4 *)xmin)[i] = e;
-            ((uint4 *)xmax)[i] = z;
-            ((uint4 *)rows)[i] = z;
-        }
+    __device__ __forceinline__ void reset(int e) const {
+        key[e] = EMPTY;
+        area[e] = 0u;
+        sx[e] = 0u;
+        sy[e] = 0u;
+        xmin[e] = EMPTY;
+        xmax[e] = 0u;
+        rows[e] = 0u;
     }
     // false when the probes found no free entry (the caller adds to the
     // global record directly)
     __device__ __forceinline__ bool push(uint32_t id, uint32_t a, uint32_t lsx, uint32_t lsy, uint32_t lx0,
                                          uint32_t lx1, uint32_t rmask) const {
-        constexpr int BITS = N == 1024 ? 10 : 9;
-        static_assert(N == 1024 || N == 512, "table sizes");
         const uint32_t h = (id * 2654435761u) >> (32 - BITS);
         for (int probe = 0; probe < 16; ++probe) {
             const int e = (int)((h + probe) & (N - 1));
@@ -162,200 +122,194 @@ __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e)
     asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e));
 }
 
+__device__ __forceinline__ void cp_async16_w(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all_w() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Run record fields (see Scratch::run_root).
+__device__ __forceinline__ int rec_root(uint32_t v) { return (int)(v >> 16); }
+__device__ __forceinline__ int rec_pix(uint32_t v) { return (int)((v >> 1) & 0x7FFFu); }
+
+// The bit-plane words of one tile held by one thread (two words), loaded
+// one tile ahead.
+struct PlaneRegs {
+    uint32_t c[2], nb[2];
+    int seg[2], seg_first;
+};
+
+// One CTA per tile at a time. Thread 0 claims tiles three ahead and copies
+// the headers and counts of the tile after next into shared memory; the bit
+// planes of the next tile are loaded into registers while the CTA works on
+// the current one.
 template <int TH>
-__global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_write(Batch B) {
-    constexpr int MAXR = WriteCfg<TH>::MAXR, MAXID = WriteCfg<TH>::MAXID;
-    constexpr int NTHREADS = WriteCfg<TH>::THREADS;
-    constexpr int NWARPS = NTHREADS / 32;
+__global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(Batch B) {
+    using C = WriteCfg<TH>;
+    constexpr int NT = C::NT, NW = NT / 32, NWD = TH * WPR, MAXR = C::MAXR, MAXID = C::MAXID;
+    constexpr int HN = 1 << C::HASH_BITS;
+    static_assert(NWD == 2 * NT, "two words per thread");
     extern __shared__ __align__(16) unsigned char smem[];
-    // feature records of the local roots, structure of arrays (tile-local x, y)
+    // feature records of the multi-run roots, structure of arrays (tile-local x, y)
     uint32_t *sArea = (uint32_t *)smem;
     uint32_t *sSx = sArea + MAXR;
     uint32_t *sSy = sSx + MAXR;
     uint32_t *sX0 = sSy + MAXR;
     uint32_t *sX1 = sX0 + MAXR;
-    uint32_t *sRows = sX1 + MAXR;                                 // bit r: a run on row r
-    int32_t *sId = (int32_t *)(sRows + MAXR);                     // node id per local root
-    uint32_t *sBrd = (uint32_t *)(sId + MAXID);                   // bit k: root k touches a tile edge
-    int32_t *sRid = (int32_t *)(sBrd + MAXID / 32);               // per warp: node id per run of a row
-    uint32_t(*sC)[WPR] = (uint32_t(*)[WPR])(sRid + NWARPS * TW);
-    uint32_t(*sE)[WPR] = sC + TH;
-    uint32_t(*sNB)[WPR] = sE + TH;
-    uint16_t(*sRunPre)[WPR] = (uint16_t(*)[WPR])(sNB + TH);
-    uint16_t(*sNBPre)[WPR] = sRunPre + TH;
-    __shared__ int sRowN[TH], sRowSeg[TH];                 // runs, first node
-    __shared__ int sRowBase[TH];                           // run ordinal of the row's first run
-    __shared__ int sT[2], sOk[2], sCap[2], sAbort;
-    __shared__ TileHdr sHdr[2];
-    __shared__ int4 sSt[2];
-    __shared__ __align__(8) uint64_t sHBar;
+    uint32_t *sRows = sX1 + MAXR;                      // bit r: a run on row r
+    int32_t *sId = (int32_t *)(sRows + MAXR);          // node id per root ordinal
+    uint32_t *sC = (uint32_t *)(sId + MAXID);          // [TH][WPR] colour bits
+    uint32_t *sE = sC + NWD;                           // [TH][WPR] run starts
+    uint32_t *sNB = sE + NWD;                          // [TH][WPR] first pixels of nodes
+    uint32_t *hmem = sNB + NWD;                        // combining table
+    uint16_t *sOrd = (uint16_t *)(hmem + 7 * HN);      // [NWD + 8] first run ordinal of each word
+    uint16_t *sNBPre = sOrd + NWD + 8;                 // [NWD] node bits before the word in its row
+    __shared__ int sT[3], sRowTot[TH], sRowSeg[TH], sCap;
+    __shared__ TileHdr sHdr[3];
+    __shared__ int4 sSt[3];
+    const TileHash<C::HASH_BITS> H(hmem);
 
-    // the combining table reuses the run buffers once the rows are written
-    const TileHash<(TH == 32 ? 1024 : 512)> H(sRid);
-    static_assert((TH == 32 ? 1024 : 512) * 7 <= NWARPS * TW, "table fits the run buffers");
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // thread 0: bulk-copy the header and counts of tile tn into slot `slot`
-    // (tiles are claimed one ahead, so the copy lands during the tile before)
-    auto fetch = [&](int tn, int slot) {
-        sT[slot] = tn;
-        if (tn < B.n_tiles) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&sHBar, (uint32_t)(sizeof(TileHdr) + sizeof(int4)));
-            bulk_g2s(&sHdr[slot], B.s.thdr + tn, (uint32_t)sizeof(TileHdr), &sHBar);
-            bulk_g2s(&sSt[slot], B.s.tstat + tn, (uint32_t)sizeof(int4), &sHBar);
-        }
-    };
-    if (threadIdx.x == 0) {
-        mbar_init(&sHBar, 1);
-        sAbort = 0;
-        sOk[0] = sOk[1] = 1;
-        sCap[0] = sCap[1] = 0;
-    }
-    __syncthreads();
-    int claim = 0;
-    if (threadIdx.x == 0) {
-        fetch(atomicAdd(&B.s.work[3], 1), 0);
-        claim = atomicAdd(&B.s.work[3], 1);
-    }
-    __syncthreads();
-    uint32_t phase = 0;
-    // Per-tile flags alternate between two slots, so that thread 0 can read
-    // and reset the slot of one tile while the others start the next: the
-    // loop needs no barrier at its top or end.
-    for (int q = 0;; q ^= 1) {
-        const int t = sT[phase];   // written before the previous tile's barriers
-        if (t >= B.n_tiles) break;
-        if (!mbar_wait(&sHBar, phase)) atomicOr(&sAbort, 1);
-        __syncthreads();
-        if (sAbort) {
-            // the header copy did not complete: wait once more (bounded) and stop
-            if (threadIdx.x == 0) {
-                mbar_wait(&sHBar, phase);
-                atomicOr(B.s.status, ST_ITER);
+    auto load_planes = [&](const TileHdr &h, PlaneRegs &p) {
+        const int64_t rowwords = (int64_t)h.TX * WPR;
+        const int64_t plane0 = (h.seg0 + (int64_t)h.y0 * h.TX + h.tx) * WPR;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int r = warp + j * NW;
+            p.c[j] = p.nb[j] = 0u;
+            p.seg[j] = 0;
+            if (r < h.th) {
+                p.c[j] = B.s.fgbits[plane0 + r * rowwords + lane];
+                p.nb[j] = B.s.nodebits[plane0 + r * rowwords + lane];
+                if (lane == 0) p.seg[j] = B.s.seg_base[h.seg0 + (int64_t)(h.y0 + r) * h.TX + h.tx];
             }
-            break;
         }
-        const TileHdr &h = sHdr[phase];
-        const int4 st = sSt[phase];
-        phase ^= 1u;
-        if (threadIdx.x == 0) {
-            fetch(claim, (int)phase);
-            claim = atomicAdd(&B.s.work[3], 1);
+        p.seg_first = lane == 0 ? B.s.seg_base[h.seg0] : 0;
+    };
+
+    int nc = 0;   // thread 0: the tile claimed for two iterations on
+    if (tid == 0) {
+        const int t0 = atomicAdd(&B.s.work[3], 1);
+        const int t1 = atomicAdd(&B.s.work[3], 1);
+        sT[0] = t0;
+        sT[1] = t1;
+        if (t0 < B.n_tiles) {
+            sHdr[0] = B.s.thdr[t0];
+            sSt[0] = B.s.tstat[t0];
         }
+        if (t1 < B.n_tiles) {
+            sHdr[1] = B.s.thdr[t1];
+            sSt[1] = B.s.tstat[t1];
+        }
+        nc = atomicAdd(&B.s.work[3], 1);
+        sCap = 0;
+    }
+    for (int e = tid; e < HN; e += NT) H.reset(e);
+    __syncthreads();
+    PlaneRegs pr;
+    if (sT[0] < B.n_tiles) load_planes(sHdr[0], pr);
+
+    for (int slot = 0;;) {
+        const int s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
+        const int t = sT[slot];
+        if (t >= B.n_tiles) break;
+        const int tn = sT[s1];
+        // thread 0: the header and counts of the tile after next (claimed one
+        // iteration ago) into the free slot, and the next claim; both are
+        // waited for before the tile's last barrier
+        int cur_claim = 0;
+        if (tid == 0) {
+            cur_claim = nc;
+            if (nc < B.n_tiles) {
+                for (int k = 0; k < (int)(sizeof(TileHdr) / 16); ++k)
+                    cp_async16_w((char *)&sHdr[s2] + 16 * k, (const char *)(B.s.thdr + nc) + 16 * k);
+                cp_async16_w(&sSt[s2], B.s.tstat + nc);
+            }
+            nc = atomicAdd(&B.s.work[3], 1);
+        }
+        const TileHdr &h = sHdr[slot];
+        const int4 st = sSt[slot];
         const int img = h.img;
         const ImgDesc &d = B.desc[img];
-        const int tx = h.tx, y0 = h.y0, x0 = h.x0, th = h.th, tw = h.tw;
-        const int64_t rowwords = (int64_t)h.TX * WPR;
-        const int64_t plane0 = (h.seg0 + (int64_t)y0 * h.TX + tx) * WPR;
+        const int y0 = h.y0, x0 = h.x0, th = h.th, tw = h.tw;
         const int64_t cap = d.cap;
         const int n_img = B.n_img;
         const int n_multi = st.y & 0xFFFF, n_roots = n_multi + (int)((uint32_t)st.y >> 16);
-        const uint16_t *rr = B.s.run_root + h.px;
+        const uint32_t *rr = B.s.run_root + h.px;
         const uint32_t *ri = B.s.rootinfo + h.px;
         const uint32_t slot0 = (uint32_t)(n_img + h.b);
-        const int vcnt = min(max(tw - 32 * lane, 0), 32);
-        const uint32_t vm = vcnt >= 32 ? FULL : ((1u << vcnt) - 1u);
-        bool ok = true, over = false;
+        bool over = false;
 
         // ---- bit planes of the tile: colour, run starts, node first-pixels
-        // (all of this warp's rows are loaded before any is used)
-        constexpr int RPW = TH / NWARPS;   // rows per warp
-        uint32_t cw[RPW], nbw[RPW];
-        int segw[RPW];
+        int rex[2];
 #pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-            const int r = warp + i * NWARPS;
-            cw[i] = nbw[i] = 0u;
-            segw[i] = 0;
-            if (r < th) {
-                cw[i] = B.s.fgbits[plane0 + r * rowwords + lane];
-                nbw[i] = B.s.nodebits[plane0 + r * rowwords + lane];
-                if (lane == 0) segw[i] = B.s.seg_base[h.seg0 + (int64_t)(y0 + r) * h.TX + tx];
-            }
-        }
-        const int seg_first = lane == 0 ? B.s.seg_base[h.seg0] : 0;
-        // node ids of the tile's border roots (their slots are consecutive),
-        // fetched while the planes are scanned; the run buffers hold them
-        // until the rows reuse that memory
-        int32_t *sBid = sRid;
-        for (int kb = threadIdx.x; kb < st.z; kb += NTHREADS) {
-            const uint32_t root = (uint32_t)B.s.gp[slot0 + kb];
-            sBid[kb] = root < (uint32_t)n_img ? 0 : B.s.canon[root];
-        }
-#pragma unroll
-        for (int i = 0; i < RPW; ++i) {
-            const int r = warp + i * NWARPS;
-            const uint32_t c = cw[i], nb = nbw[i];
-            const uint32_t vr = r < th ? vm : 0u;
+        for (int j = 0; j < 2; ++j) {
+            const int r = warp + j * NW, word = tid + j * NT;
+            const uint32_t c = pr.c[j];
+            const int vcnt = min(max(tw - 32 * lane, 0), 32);
+            const uint32_t vr = r < th ? (vcnt >= 32 ? FULL : ((1u << vcnt) - 1u)) : 0u;
             const uint32_t left = __shfl_up_sync(FULL, c, 1);
             const uint32_t prev = (c << 1) | (lane ? (left >> 31) : 0u);
             const uint32_t e = ((c ^ prev) | (lane == 0 ? 1u : 0u)) & vr;
-            sC[r][lane] = c;
-            sE[r][lane] = e;
-            sNB[r][lane] = nb;
-            int tot;
-            sRunPre[r][lane] = (uint16_t)warp_excl_sum(__popc(e), &tot);
-            if (lane == 0) sRowN[r] = tot;
-            int ntot;
-            sNBPre[r][lane] = (uint16_t)warp_excl_sum(__popc(nb), &ntot);
-            if (lane == 0) sRowSeg[r] = r < th ? segw[i] - seg_first : 0;
+            sC[word] = c;
+            sE[word] = e;
+            sNB[word] = pr.nb[j];
+            int ntot, rtot;
+            sNBPre[word] = (uint16_t)warp_excl_sum(__popc(pr.nb[j]), &ntot);
+            rex[j] = warp_excl_sum(__popc(e), &rtot);
+            if (lane == 0) {
+                sRowTot[r] = rtot;
+                sRowSeg[r] = r < th ? pr.seg[j] - pr.seg_first : 0;
+            }
         }
         __syncthreads();
+        // the planes of the next tile (its header landed one tile ago)
+        if (tn < B.n_tiles) load_planes(sHdr[s1], pr);
+        int n;   // runs of the tile
         {
-            // every warp scans the run counts itself and keeps the prefixes
-            // of its own rows (saves a barrier)
-            int tot;
-            const int es = warp_excl_sum(lane < TH ? sRowN[lane] : 0, &tot);
-            if (lane < TH && lane % NWARPS == warp) sRowBase[lane] = es;
-            __syncwarp();
+            int wt;
+            const int ex = warp_excl_sum(lane < TH ? sRowTot[lane] : 0, &wt);
+            n = wt;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int r = warp + j * NW;
+                sOrd[tid + j * NT] = (uint16_t)(__shfl_sync(FULL, ex, r) + rex[j]);
+            }
+            if (tid == 0) sOrd[NWD] = (uint16_t)n;
+        }
+        for (int k = tid; k < min(n_multi, MAXR); k += NT) {
+            sArea[k] = 0u;
+            sSx[k] = 0u;
+            sSy[k] = 0u;
+            sX0[k] = 0xFFFFu;
+            sX1[k] = 0u;
+            sRows[k] = 0u;
         }
 
-        // node id of a local root; the border roots' ids are in sBid until
-        // the rows phase
-        auto root_id_early = [&](uint32_t info) -> int {
-            const int idx = info & 0xFFFF;
-            if (!((info >> 17) & 1u)) {
-                const int r = idx >> 10, c = idx & 1023, l = c >> 5;
-                return 1 + sRowSeg[r] + sNBPre[r][l] + __popc(sNB[r][l] & mask_lt(c & 31));
-            }
-            return sBid[(info >> 18) & 0xFFFu];
-        };
+        // node id of a local root (rootinfo: its first pixel, border flag and
+        // border ordinal)
         auto root_id = [&](uint32_t info) -> int {
             const int idx = info & 0xFFFF;
             if (!((info >> 17) & 1u)) {
-                const int r = idx >> 10, c = idx & 1023, l = c >> 5;
-                return 1 + sRowSeg[r] + sNBPre[r][l] + __popc(sNB[r][l] & mask_lt(c & 31));
+                const int r = idx >> 10, c = idx & 1023, wi = r * WPR + (c >> 5);
+                return 1 + sRowSeg[r] + (int)sNBPre[wi] + __popc(sNB[wi] & mask_lt(c & 31));
             }
             const uint32_t root = (uint32_t)B.s.gp[slot0 + ((info >> 18) & 0xFFFu)];
             return root < (uint32_t)n_img ? 0 : B.s.canon[root];
         };
+        auto id_of = [&](int k) -> int { return k < MAXID ? sId[k] : root_id(ri[k]); };
+        // ordinal of the run covering column x of row r
+        auto ord_at = [&](int r, int x) -> int {
+            const int wi = r * WPR + (x >> 5);
+            return (int)sOrd[wi] + __popc(sE[wi] & mask_le(x & 31)) - 1;
+        };
 
-        // ---- node ids, edge flags and feature records of the local roots
-        uint32_t info_next = warp * 32 + lane < n_roots ? ri[warp * 32 + lane] : 0u;   // one iteration ahead
-        for (int k0 = warp * 32; k0 < n_roots; k0 += NTHREADS) {
-            const int k = k0 + lane;
-            const bool valid = k < n_roots;
-            const uint32_t info = info_next;
-            if (k + NTHREADS < n_roots) info_next = ri[k + NTHREADS];
-            const bool isb = (info >> 17) & 1u;
-            const bool multi = k < n_multi;
-            const bool spill = valid && multi && k >= MAXR && !isb;
-            int id = 0;
-            if (valid && (k < MAXID || spill)) id = root_id_early(info);
-            if (k0 < MAXID) {
-                const uint32_t bal = __ballot_sync(FULL, valid && isb);
-                if (lane == 0) sBrd[k0 >> 5] = bal;
-                if (valid) sId[k] = id;
-            }
-            if (valid && multi && k < MAXR) {
-                sArea[k] = 0u;
-                sSx[k] = 0u;
-                sSy[k] = 0u;
-                sX0[k] = 0xFFFFu;
-                sX1[k] = 0u;
-                sRows[k] = 0u;
-            } else if (spill && id < cap) {
+        // ---- node ids of the roots; global records of spilled multi-run roots
+        for (int k = tid; k < n_roots; k += NT) {
+            const uint32_t info = ri[k];
+            const int id = root_id(info);
+            if (k < MAXID) sId[k] = id;
+            if (k < n_multi && k >= MAXR && !((info >> 17) & 1u) && id < cap) {
                 d.feat[0 * cap + id] = 0;
                 d.feat[1 * cap + id] = INT64_MAX;
                 d.feat[2 * cap + id] = y0 + ((info & 0xFFFF) >> 10);
@@ -367,193 +321,157 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
         }
         __syncthreads();
 
-        // ---- rows: run features, tree parents of the row below, label rows
-        const bool labels = B.labels && d.fg != nullptr;
-        constexpr int PF = 4;
-        int pf[PF];
-        int pf_row = -1;
-        for (int r = warp; r < th; r += NWARPS) {
-            const uint32_t e = sE[r][lane];
-            const int row_slot = sRowBase[r], nr = sRowN[r];
-            int32_t *rid = sRid + warp * TW;
-            // root ordinals of the row's runs (rid: by run index within the
-            // row); the first PF rounds were fetched into registers while the
-            // warp worked on its previous row
-#pragma unroll
-            for (int j = 0; j < PF; ++j) {
-                const int i = lane + 32 * j;
-                if (i < nr) rid[swz(i)] = pf_row == r ? pf[j] : (int)rr[row_slot + i];
-            }
-            // the rest in groups of 8 loads in flight
-            for (int i0 = lane + 32 * PF; i0 < nr; i0 += 8 * 32) {
-                int v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = i0 + 32 * u < nr ? (int)rr[row_slot + i0 + 32 * u] : 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i0 + 32 * u < nr) rid[swz(i0 + 32 * u)] = v[u];
-            }
-            {
-                const int rn = r + NWARPS;   // this warp's next row
-                if (rn < th) {
-                    const int nb = sRowBase[rn], nn = sRowN[rn];
-#pragma unroll
-                    for (int j = 0; j < PF; ++j) {
-                        const int i = lane + 32 * j;
-                        pf[j] = i < nn ? (int)rr[nb + i] : 0;
-                    }
-                    pf_row = rn;
-                }
-            }
-            __syncwarp();
-            // each lane walks the runs starting in its word. Along a row the
-            // runs alternate colours, so a component crossing the row many
-            // times (the percolating one of a dense random image) owns every
-            // other run: one register accumulator per run parity sums its
-            // runs, and the shared record is updated only when the root changes.
-            {
-                const int first = e ? 32 * lane + __ffs(e) - 1 : TW;
-                const int nxt = min(warp_suffix_min_excl(first, TW), tw);
-                int q = sRunPre[r][lane];
-                uint32_t m = e;
-                RunAcc acc0, acc1;
-                auto flush = [&](const RunAcc &a) {
-                    // single-run roots (k >= n_multi) need no accumulation:
-                    // the feature pass reads their run from the bit planes
-                    if (a.k < 0 || a.k >= n_multi) return;
-                    if (a.k < MAXR) {
-                        // results unused: reductions, the lane does not wait
-                        atomicAdd(&sArea[a.k], a.len);
-                        atomicAdd(&sSx[a.k], a.sx);
-                        atomicAdd(&sSy[a.k], (uint32_t)r * a.len);
-                        atomicMin(&sX0[a.k], (uint32_t)a.x0);
-                        atomicMax(&sX1[a.k], (uint32_t)a.x1);
-                        atomicOr(&sRows[a.k], 1u << r);
-                    } else {
-                        const int id = root_id(ri[a.k]);
-                        if (id < cap)
-                            feat_add(d.feat, cap, id, a.len, a.sx + (unsigned long long)x0 * a.len,
-                                     (unsigned long long)(y0 + r) * a.len, x0 + a.x0, y0 + r, x0 + a.x1, y0 + r);
-                    }
-                };
-                // one run into the accumulator of its parity (the caller
-                // alternates acc0 / acc1 statically)
-                auto step = [&](RunAcc &acc) {
-                    const int xs = 32 * lane + __ffs(m) - 1;
-                    m &= m - 1;
-                    const int xe = m ? 32 * lane + __ffs(m) - 1 : nxt;
-                    const int k = rid[swz(q)];
-                    rid[swz(q)] = k < MAXID ? sId[k] : root_id(ri[k]);
-                    if (k == acc.k) {
-                        acc.add(xs, xe);
-                    } else {
-                        flush(acc);
-                        acc.start(k, xs, xe);
-                    }
-                    ++q;
-                };
-                if ((q & 1) && m) step(acc1);
-                while (m) {
-                    step(acc0);
-                    if (!m) break;
-                    step(acc1);
-                }
-                // the last accumulators of neighbouring lanes often hold the
-                // same root (a component crossing the row many times): combine
-                // equal roots of consecutive lanes, then the last lane of each
-                // group flushes
-                warp_combine(acc0, lane);
-                warp_combine(acc1, lane);
-                flush(acc0);
-                flush(acc1);
-            }
-            __syncwarp();
-            // nodes whose first pixel is on row r + 1: parent = node of the
-            // pixel above (the initial adjacency of Algorithm 2)
-            if (r + 1 < th) {
-                const uint32_t nb = sNB[r + 1][lane];
-                uint32_t m = nb;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int id = 1 + sRowSeg[r + 1] + sNBPre[r + 1][lane] + __popc(nb & mask_lt(b));
-                    const int p = rid[swz(sRunPre[r][lane] + __popc(e & mask_le(b)) - 1)];
-                    if (id < cap) {
-                        d.parent[id] = p;
-                        if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[r + 1][lane] >> b) & 1u);
-                    } else {
-                        over = true;
-                    }
-                }
-            }
-            if (labels) {
+        // ---- label rows (each warp its two rows, 4 pixels per lane per step)
+        if (B.labels && d.fg != nullptr) {
+#pragma unroll 1
+            for (int j = 0; j < 2; ++j) {
+                const int r = warp + j * NW;
+                if (r >= th) break;
                 int32_t *fgrow = d.fg + (int64_t)(y0 + r) * h.w + x0;
                 int32_t *bgrow = d.bg + (int64_t)(y0 + r) * h.w + x0;
+                constexpr int G = TW / 128, GB = 4;   // groups per lane, groups per batch
+#pragma unroll 1
+                for (int g0 = 0; g0 < G; g0 += GB) {
+                    int q0[GB];
+                    uint32_t v0[GB];
 #pragma unroll
-                for (int k8 = 0; k8 < TW / 128; ++k8) {
-                    const int x = 128 * k8 + 4 * lane;
-                    if (x < tw) {
-                        const int wl = x >> 5, b = x & 31;
-                        const uint32_t ew = sE[r][wl], cw = sC[r][wl];
-                        // run index of the group's first pixel, and run starts
-                        // inside the group (usually none: one lookup)
-                        const int q0 = sRunPre[r][wl] - 1 + __popc(ew & mask_le(b));
+                    for (int u = 0; u < GB; ++u) {
+                        const int x = 128 * (g0 + u) + 4 * lane;
+                        q0[u] = x < tw ? ord_at(r, x) : -1;
+                        v0[u] = q0[u] >= 0 ? rr[q0[u]] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < GB; ++u) {
+                        if (q0[u] < 0) continue;
+                        const int x = 128 * (g0 + u) + 4 * lane;
+                        const int wi = r * WPR + (x >> 5), b = x & 31;
+                        const uint32_t ew = sE[wi], cw = sC[wi];
+                        // run starts inside the group (usually none: one lookup)
                         const uint32_t s3 = (ew >> (b + 1)) & 7u, c4 = (cw >> b) & 15u;
                         int id[4];
-                        id[0] = rid[swz(q0)];
+                        id[0] = id_of(rec_root(v0[u]));
                         if (s3 == 0u) {
                             id[1] = id[2] = id[3] = id[0];
                         } else {
-                            const int q1 = q0 + (int)(s3 & 1u), q2 = q1 + (int)((s3 >> 1) & 1u),
+                            const int q1 = q0[u] + (int)(s3 & 1u), q2 = q1 + (int)((s3 >> 1) & 1u),
                                       q3 = q2 + (int)(s3 >> 2);
-                            id[1] = rid[swz(q1)];
-                            id[2] = rid[swz(q2)];
-                            id[3] = rid[swz(q3)];
+                            id[1] = id_of(rec_root(rr[q1]));
+                            id[2] = id_of(rec_root(rr[q2]));
+                            id[3] = id_of(rec_root(rr[q3]));
                         }
                         int fv[4], bv[4];
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const bool isfg = (c4 >> j) & 1u;
-                            fv[j] = isfg ? id[j] : -1;
-                            bv[j] = isfg ? -1 : id[j];
+                        for (int i = 0; i < 4; ++i) {
+                            const bool isfg = (c4 >> i) & 1u;
+                            fv[i] = isfg ? id[i] : -1;
+                            bv[i] = isfg ? -1 : id[i];
                         }
                         if (d.vec) {
                             st_cs_v4(fgrow + x, fv[0], fv[1], fv[2], fv[3]);
                             st_cs_v4(bgrow + x, bv[0], bv[1], bv[2], bv[3]);
                         } else {
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                if (x + j < tw) {
-                                    fgrow[x + j] = fv[j];
-                                    bgrow[x + j] = bv[j];
+                            for (int i = 0; i < 4; ++i) {
+                                if (x + i < tw) {
+                                    fgrow[x + i] = fv[i];
+                                    bgrow[x + i] = bv[i];
                                 }
                             }
                         }
                     }
                 }
             }
-            __syncwarp();
         }
-        // nodes whose first pixel is on the tile's top row: the pixel above is
-        // in the tile above (or outside the image: the exterior)
-        if (warp == NWARPS - 1) {
-            const uint32_t nb = sNB[0][lane];
-            uint32_t m = nb;
+
+        // ---- run features of the multi-run roots (one thread per run, 32
+        // consecutive runs per warp). Along a row the runs alternate colours,
+        // so the runs of one component crossing the row many times sit two
+        // lanes apart: a segmented scan along such stride-2 chains of equal
+        // (root, row) sums them, and only the chain's last lane updates the
+        // shared record.
+        for (int i0 = 0; i0 < n; i0 += NT) {
+            const int i = i0 + tid;
+            const uint32_t v = i < n ? rr[i] : 0xFFFFFFFFu;
+            // the next run's start: the next lane's record (the last lane loads it)
+            uint32_t vn = __shfl_down_sync(FULL, v, 1);
+            if (lane == 31) vn = i + 1 < n ? rr[i + 1] : 0xFFFFFFFFu;
+            const int k = rec_root(v), pix = rec_pix(v), r = pix >> 10, s = pix & (TW - 1);
+            const bool multi = i < n && k < n_multi;
+            int en = tw;
+            if (i + 1 < n) {
+                const int pn = rec_pix(vn);
+                if ((pn >> 10) == r) en = pn & (TW - 1);
+            }
+            uint32_t len = 0, sx = 0;
+            uint32_t key = 0xFFFFFFFFu;   // (root, row) of a multi-run root on chip
+            if (multi) {
+                len = (uint32_t)(en - s);
+                sx = (uint32_t)((s + en - 1) * (en - s) / 2);
+                if (k < MAXR) {
+                    key = ((uint32_t)k << 5) | (uint32_t)r;
+                } else {
+                    const int id = id_of(k);
+                    if (id < cap)
+                        feat_add(d.feat, cap, id, len, sx + (unsigned long long)x0 * len,
+                                 (unsigned long long)(y0 + r) * len, x0 + s, y0 + r, x0 + en - 1, y0 + r);
+                }
+            }
+            const uint32_t kprev = __shfl_up_sync(FULL, key, 2);
+            const bool cont = lane >= 2 && key != 0xFFFFFFFFu && kprev == key;
+            int head = cont ? 0 : lane;   // lane of this chain's first run
+#pragma unroll
+            for (int dd = 2; dd < 32; dd <<= 1) {
+                const int hu = __shfl_up_sync(FULL, head, dd);
+                if (lane >= dd) head = max(head, hu);   // even offsets: the same parity
+            }
+#pragma unroll
+            for (int dd = 2; dd < 32; dd <<= 1) {
+                const uint32_t tl = __shfl_up_sync(FULL, len, dd), ts = __shfl_up_sync(FULL, sx, dd);
+                if (lane - dd >= head) {
+                    len += tl;
+                    sx += ts;
+                }
+            }
+            const int xs0 = __shfl_sync(FULL, s, head);
+            const bool cont_next = __shfl_down_sync(FULL, (int)cont, 2) != 0;
+            if (key != 0xFFFFFFFFu && !(lane < 30 && cont_next)) {
+                const int kk = (int)(key >> 5);
+                // results unused: reductions, the lane does not wait
+                atomicAdd(&sArea[kk], len);
+                atomicAdd(&sSx[kk], sx);
+                atomicAdd(&sSy[kk], (uint32_t)r * len);
+                atomicMin(&sX0[kk], (uint32_t)xs0);
+                atomicMax(&sX1[kk], (uint32_t)(en - 1));
+                atomicOr(&sRows[kk], 1u << r);
+            }
+        }
+
+        // ---- tree: nodes whose first pixel lies in this thread's words;
+        // parent = node of the pixel above (the initial adjacency of
+        // Algorithm 2), from the row above or, on the tile's top row, from the
+        // tile above (or the exterior on the image's top row)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int r = warp + j * NW, word = tid + j * NT;
+            const uint32_t nbw = sNB[word];
+            uint32_t m = nbw;
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
                 const int c = 32 * lane + b;
-                const int id = 1 + sRowSeg[0] + sNBPre[0][lane] + __popc(nb & mask_lt(b));
+                const int id = 1 + sRowSeg[r] + (int)sNBPre[word] + __popc(nbw & mask_lt(b));
                 int p = 0;
-                if (y0 > 0) {
+                if (r > 0) {
+                    p = id_of(rec_root(rr[ord_at(r - 1, c)]));
+                } else if (y0 > 0) {
                     // the bottom edge cell of the tile above, same column
-                    const uint32_t s2 = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
-                    const uint32_t root = (uint32_t)B.s.gp[s2];
+                    const uint32_t s2b = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
+                    const uint32_t root = (uint32_t)B.s.gp[s2b];
                     p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
                 }
                 if (id < cap) {
                     d.parent[id] = p;
-                    if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[0][lane] >> b) & 1u);
+                    if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[word] >> b) & 1u);
                 } else {
                     over = true;
                 }
@@ -561,20 +479,15 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
         }
         __syncthreads();
 
-        // ---- per local root: features (records of multi-run roots; the
-        // run itself for a single-run root)
-        H.init(threadIdx.x, NTHREADS);
-        __syncthreads();
-        uint32_t fin_next = threadIdx.x < n_roots ? ri[threadIdx.x] : 0u;   // one iteration ahead
-        for (int k = threadIdx.x; k < n_roots; k += NTHREADS) {
-            const uint32_t info = fin_next;
-            if (k + NTHREADS < n_roots) fin_next = ri[k + NTHREADS];
+        // ---- per local root: features (records of multi-run roots; the run
+        // itself for a single-run root)
+        for (int k = tid; k < n_roots; k += NT) {
             if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
+            const uint32_t info = ri[k];
             const int idx = info & 0xFFFF, r = idx >> 10, c = idx & 1023;
             const bool isb = (info >> 17) & 1u;
-            const int id = k < MAXID ? sId[k] : root_id(info);
+            const int id = id_of(k);
             if (id >= cap) continue;
-            // tile-relative features first
             uint32_t la, lsx, lsy, lx0, lx1, rmask;
             if (k < n_multi) {
                 la = sArea[k];
@@ -584,11 +497,14 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
                 lx1 = sX1[k];
                 rmask = sRows[k];
             } else {
-                // the run starting at (r, c) ends before the next run start
-                int l = c >> 5;
-                uint32_t m = sE[r][l] & ~mask_le(c & 31);
-                while (!m && ++l < WPR) m = sE[r][l];
-                const int ce = m ? min(32 * l + __ffs(m) - 1, tw) : tw;
+                // the run starting at (r, c) ends where the next run of the
+                // row starts
+                const int qr = ord_at(r, c);
+                int ce = tw;
+                if (qr + 1 < n) {
+                    const int pn = rec_pix(rr[qr + 1]);
+                    if ((pn >> 10) == r) ce = pn & (TW - 1);
+                }
                 la = (uint32_t)(ce - c);
                 lsx = (uint32_t)((c + ce - 1) * (ce - c) / 2);
                 lsy = (uint32_t)r * la;
@@ -598,7 +514,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
             }
             if (isb && H.push((uint32_t)id, la, lsx, lsy, lx0, lx1, rmask)) continue;
             const long long area = la;
-            const long long sx = (long long)lsx + area * x0, sy = (long long)lsy + area * y0;
+            const long long sxg = (long long)lsx + area * x0, syg = (long long)lsy + area * y0;
             const int xmin = x0 + (int)lx0, xmax = x0 + (int)lx1;
             const int ymin = y0 + __ffs(rmask) - 1, ymax = y0 + 31 - __clz(rmask);
             if (!isb) {
@@ -607,38 +523,44 @@ __global__ void __launch_bounds__(WriteCfg<TH>::THREADS, WriteCfg<TH>::CTAS) k_w
                 d.feat[2 * cap + id] = ymin;
                 d.feat[3 * cap + id] = xmax;
                 d.feat[4 * cap + id] = ymax;
-                d.feat[5 * cap + id] = sx;
-                d.feat[6 * cap + id] = sy;
+                d.feat[5 * cap + id] = sxg;
+                d.feat[6 * cap + id] = syg;
             } else {
-                feat_add(d.feat, cap, id, (unsigned long long)area, (unsigned long long)sx, (unsigned long long)sy,
+                feat_add(d.feat, cap, id, (unsigned long long)area, (unsigned long long)sxg, (unsigned long long)syg,
                          xmin, ymin, xmax, ymax);
             }
         }
-        if (!ok) atomicAnd(&sOk[q], 0);
-        if (over) atomicOr(&sCap[q], 1);
+        if (over) atomicOr(&sCap, 1);
+        if (tid == 0) {
+            cp_async_wait_all_w();   // the header and counts of the tile after next
+            sT[s2] = cur_claim;
+        }
         __syncthreads();
-        for (int e = threadIdx.x; e < (TH == 32 ? 1024 : 512); e += NTHREADS) {
-            const uint32_t id = H.key[e];
-            if (id == H.EMPTY) continue;
-            const unsigned long long a = H.area[e];
-            const uint32_t rm = H.rows[e];
-            feat_add(d.feat, cap, (int)id, a, H.sx[e] + a * (unsigned long long)x0, H.sy[e] + a * (unsigned long long)y0,
-                     x0 + (int)H.xmin[e], y0 + __ffs(rm) - 1, x0 + (int)H.xmax[e], y0 + 31 - __clz(rm));
+        // the combining table: flush into the node records, then clear
+        for (int e2 = tid; e2 < HN; e2 += NT) {
+            const uint32_t id = H.key[e2];
+            if (id != H.EMPTY) {
+                const unsigned long long a = H.area[e2];
+                const uint32_t rm = H.rows[e2];
+                feat_add(d.feat, cap, (int)id, a, H.sx[e2] + a * (unsigned long long)x0,
+                         H.sy[e2] + a * (unsigned long long)y0, x0 + (int)H.xmin[e2], y0 + __ffs(rm) - 1,
+                         x0 + (int)H.xmax[e2], y0 + 31 - __clz(rm));
+                H.reset(e2);
+            }
         }
-        if (threadIdx.x == 0) {
-            if (!sOk[q]) set_status(B, d, ST_ITER);
-            if (sCap[q]) set_status(B, d, ST_CAPACITY);
-            sOk[q] = 1;   // the slot is next used two tiles on
-            sCap[q] = 0;
+        if (tid == 0) {
+            if (sCap) set_status(B, d, ST_CAPACITY);
+            sCap = 0;
         }
+        slot = s1;
     }
 }
 
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     if (B.th == 32)
-        k_write<32><<<min(B.n_tiles, WriteCfg<32>::CTAS * c.sms), WriteCfg<32>::THREADS, write_smem<32>(), st>>>(B);
+        k_write<32><<<min(B.n_tiles, WriteCfg<32>::CTAS * c.sms), WriteCfg<32>::NT, write_smem<32>(), st>>>(B);
     else
-        k_write<16><<<min(B.n_tiles, WriteCfg<16>::CTAS * c.sms), WriteCfg<16>::THREADS, write_smem<16>(), st>>>(B);
+        k_write<16><<<min(B.n_tiles, WriteCfg<16>::CTAS * c.sms), WriteCfg<16>::NT, write_smem<16>(), st>>>(B);
 }
 
 cudaError_t configure_write() {
