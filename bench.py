@@ -152,14 +152,25 @@ class ClockSampler:
 
 
 def kernel_source_hash(name):
-    """Hash of a kernel source file's code, comments and blank space left
-    out: recorded DRAM traffic stays valid across comment-only edits."""
+    """Hash of a kernel source file's code together with the local headers it
+    includes (#include "..." in the same folder, recursively), comments and
+    blank space left out: recorded DRAM traffic stays valid across
+    comment-only edits and goes stale when the kernel or a header changes."""
     import re
-    text = open(os.path.join(ROOT, "paper_2006_09299_gb300", "csrc", name)).read()
-    text = re.sub(r"//[^\n]*", "", text)
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    text = re.sub(r"\s+", " ", text).strip()
-    return hashlib.sha256(text.encode()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2006_09299_gb300", "csrc")
+    seen, parts, todo = set(), [], [name]
+    while todo:
+        f = todo.pop(0)
+        path = os.path.join(csrc, f)
+        if f in seen or not os.path.exists(path):
+            continue
+        seen.add(f)
+        text = open(path).read()
+        todo += re.findall(r'#include\s+"([^"/]+)"', text)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        parts.append(f + ":" + re.sub(r"\s+", " ", text).strip())
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel_file, workload, units):
@@ -329,16 +340,17 @@ def replica_throughput(ms, px, world, device):
 
 
 def pick_tile_rows(args, ctx, step, shapes):
-    """Tile height: fixed by --tile-rows, or chosen by the autotuner (a fresh
-    timing of this step under each height, CUDA events)."""
+    """Tile shape and merge schedule: the tile height fixed by --tile-rows
+    (default merge schedule), or both chosen by the autotuner (a fresh timing
+    of this step under each choice, CUDA events)."""
     from paper_2006_09299_gb300 import autotune
     if args.tile_rows != "auto":
         ctx.set_tile_rows(int(args.tile_rows))
-        return {"rows": int(args.tile_rows), "cols": 1024, "chosen_by": "flag"}
+        return {"rows": int(args.tile_rows), "cols": autotune.TILE_COLS,
+                "merge_split": autotune.MERGE_SPLITS[0], "chosen_by": "flag"}
     path = os.path.join(tempfile.mkdtemp(), "tune.json")
-    rows, times = autotune.tune(ctx, step, autotune.size_class(shapes), cache_path=path, reps=3, warmup=2)
-    return {"rows": rows, "cols": 1024, "chosen_by": "autotuner",
-            "ms_per_step": {str(k): round(v, 4) for k, v in times.items()}}
+    choice, times = autotune.tune(ctx, step, autotune.size_class(shapes), cache_path=path, reps=3, warmup=2)
+    return dict(choice, chosen_by="autotuner", ms_per_step={k: round(v, 4) for k, v in times.items()})
 
 
 def run_e2e(args, ctx, imgs, outs, dev, stream, px):
@@ -499,8 +511,8 @@ def single_image_record(ccl, dev, stream, img, w, steps, warmup, name, cpu=True)
     def labels_off():
         ctx.analyze(d_img, out=off)
 
-    rows, tune_ms = autotune.tune(ctx, analysis, autotune.size_class([(w, h)]),
-                                  cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=3, warmup=2)
+    choice, tune_ms = autotune.tune(ctx, analysis, autotune.size_class([(w, h)]),
+                                    cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=3, warmup=2)
     launches0 = ctx.launch_count()
     ms_a = timed_ms(analysis, steps, warmup, stream)
     ms_af = timed_ms(analysis_fill, steps, warmup, stream)
@@ -512,8 +524,8 @@ def single_image_record(ccl, dev, stream, img, w, steps, warmup, name, cpu=True)
     ph_off = phase_times(ctx, labels_off, steps)
     n_nodes = out.n
     rec = {
-        "workload": name, "pixels": px, "nodes": n_nodes, "tile": {"rows": rows, "cols": 1024,
-                                                                  "tuning_ms": {str(k): round(v, 4) for k, v in tune_ms.items()}},
+        "workload": name, "pixels": px, "nodes": n_nodes,
+        "tile": dict(choice, chosen_by="autotuner", tuning_ms={k: round(v, 4) for k, v in tune_ms.items()}),
         "api": "ccl_create + ccl_analyze (+ ccl_fill_holes), one image",
         "steps": steps, "warmup": warmup,
         "analysis_ms": round(ms_a, 4), "analysis_gpx_s": round(px / ms_a / 1e6, 2),
@@ -595,9 +607,9 @@ def batched_vs_plain(ccl, dev, stream, reps=5):
     outs = bctx.new_outputs(shapes, labels=True, fill=False, device=dev)
     pctx = ccl.BatchContext(1, 2048 * 2048, 2048, graph_cache=False)
     from paper_2006_09299_gb300 import autotune
-    rows, times = autotune.tune(bctx, lambda: bctx.analyze(d_imgs, outs=outs), autotune.size_class(shapes),
-                                cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=3, warmup=2)
-    pctx.set_tile_rows(rows)
+    choice, times = autotune.tune(bctx, lambda: bctx.analyze(d_imgs, outs=outs), autotune.size_class(shapes),
+                                  cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=3, warmup=2)
+    autotune.apply(pctx, choice)
 
     def batched():
         bctx.analyze(d_imgs, outs=outs)
@@ -625,7 +637,7 @@ def batched_vs_plain(ccl, dev, stream, reps=5):
             "batched_ms": round(res["batched"], 3), "plain_ms": round(res["plain"], 3),
             "batched_gpx_s": round(px / res["batched"] / 1e6, 2), "plain_gpx_s": round(px / res["plain"] / 1e6, 2),
             "ratio": round(res["plain"] / res["batched"], 2),
-            "tile_rows": rows, "tuning_ms": {str(k): round(v, 4) for k, v in times.items()}}
+            "tile": choice, "tuning_ms": {k: round(v, 4) for k, v in times.items()}}
 
 
 # ------------------------------------------------------------ reference arm

@@ -226,6 +226,15 @@ ccl_status ccl_relabel_filtered_batched(ccl_ctx *ctx, int32_t *const *d_fg_out, 
  * image (ccl.autotune picks one per size class by timing both). */
 ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows);
 
+/* Merge schedule for later analyses of this context: the number of work
+ * items that share one 32-pixel word of a boundary between two bands of
+ * tiles in the cross-tile merge (the unification of Algorithm 2 across tile
+ * edges): 1, 2, 4 (default) or 8, each item taking 32 / items_per_word of
+ * the word's columns. More items spread a dense boundary's unions over more
+ * threads; fewer have less overhead on sparse boundaries. Results are
+ * identical; ccl.autotune times the choices. Other values: CCL_ERR_ARG. */
+ccl_status ccl_set_merge_split(ccl_ctx *ctx, int32_t items_per_word);
+
 /* Enable (1) or disable (0) the CUDA-graph cache of ccl_analyze_batched and
  * ccl_analyze. */
 ccl_status ccl_set_graph_cache(ccl_ctx *ctx, int32_t enable);

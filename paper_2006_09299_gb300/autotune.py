@@ -1,16 +1,24 @@
-"""Autotuner for the tile shape of the CUDA path.
+"""Autotuner for the tile shape and merge schedule of the CUDA path.
 
-The tile is 1024 columns wide (one 32-bit word per lane); its height is 32
-or 16 rows (ccl_set_tile_rows). Taller tiles have fewer tile edges to merge
-across; shorter tiles let more CTAs share an SM and hide more latency. Which
-wins depends on the images, so the tuner times the caller's own work under
-each height with CUDA events and keeps the fastest, per size class, in a
-small JSON cache.
+Two launch choices change the speed but never the results:
+  - the tile height, 32 or 16 rows of 1024 columns (ccl_set_tile_rows):
+    taller tiles have fewer tile edges to merge across, shorter tiles let
+    more CTAs share an SM and hide more latency;
+  - the merge schedule, 1, 2, 4 or 8 work items per 32-pixel word of a
+    boundary between bands of tiles (ccl_set_merge_split): more items spread
+    a dense boundary's unions over more threads, fewer cost less on sparse
+    boundaries.
+Which wins depends on the images, so the tuner times the caller's own work
+with CUDA events: first every tile height at the default merge schedule,
+then every merge schedule at the best height, and keeps the fastest pair
+per size class in a small JSON cache.
 """
 import json
 import os
 
 TILE_ROWS = (32, 16)
+MERGE_SPLITS = (4, 1, 2, 8)      # the first is the default
+TILE_COLS = 1024
 
 
 def size_class(shapes, n_images=None):
@@ -29,7 +37,7 @@ def size_class(shapes, n_images=None):
 
 def default_cache_path():
     return os.environ.get("CCL_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "ccl_gb300",
-                                                         "tile_rows.json"))
+                                                         "tile_shape.json"))
 
 
 def _load(path):
@@ -50,32 +58,52 @@ def _store(path, data):
     os.replace(tmp, path)
 
 
+def choice_name(rows, split):
+    return "rows%d_cols%d_split%d" % (rows, TILE_COLS, split)
+
+
+def apply(ctx, choice):
+    ctx.set_tile_rows(choice["rows"])
+    if hasattr(ctx, "set_merge_split"):
+        ctx.set_merge_split(choice["merge_split"])
+
+
 def tune(ctx, run, key, cache_path=None, reps=5, warmup=2, timer=None, force=False):
-    """Pick the tile height for `run` (a callable that enqueues the work to
-    tune, e.g. one batched analysis) on context `ctx`, set it on ctx and
-    return (rows, {rows: ms}).
+    """Pick the tile shape and merge schedule for `run` (a callable that
+    enqueues the work to tune, e.g. one batched analysis) on context `ctx`,
+    set them on ctx and return (choice, {choice_name: ms}) where choice =
+    {"rows", "cols", "merge_split"}.
 
     timer(fn, reps) -> ms per call; defaults to CUDA events on the current
     stream. A cached choice for `key` is reused unless force is set."""
     path = cache_path or default_cache_path()
     data = _load(path)
-    if not force and key in data:
-        rows = int(data[key]["tile_rows"])
-        ctx.set_tile_rows(rows)
-        return rows, data[key].get("ms", {})
+    if not force and key in data and "merge_split" in data[key]:
+        choice = {"rows": int(data[key]["rows"]), "cols": TILE_COLS, "merge_split": int(data[key]["merge_split"])}
+        apply(ctx, choice)
+        return choice, data[key].get("ms", {})
     if timer is None:
         timer = cuda_timer
     times = {}
-    for rows in TILE_ROWS:
-        ctx.set_tile_rows(rows)
+
+    def measure(rows, split):
+        c = {"rows": rows, "cols": TILE_COLS, "merge_split": split}
+        apply(ctx, c)
         for _ in range(warmup):
             run()
-        times[rows] = timer(run, reps)
-    best = min(times, key=times.get)
-    ctx.set_tile_rows(best)
-    data[key] = {"tile_rows": best, "ms": {str(k): round(v, 4) for k, v in times.items()}}
+        times[choice_name(rows, split)] = timer(run, reps)
+        return times[choice_name(rows, split)]
+
+    split0 = MERGE_SPLITS[0]
+    best_rows = min(TILE_ROWS, key=lambda r: measure(r, split0))
+    splits = [split0] + [s for s in MERGE_SPLITS[1:] if hasattr(ctx, "set_merge_split")]
+    best_split = min(splits, key=lambda s: times.get(choice_name(best_rows, s)) or measure(best_rows, s))
+    choice = {"rows": best_rows, "cols": TILE_COLS, "merge_split": best_split}
+    apply(ctx, choice)
+    data[key] = {"rows": best_rows, "cols": TILE_COLS, "merge_split": best_split,
+                 "ms": {k: round(v, 4) for k, v in times.items()}}
     _store(path, data)
-    return best, times
+    return choice, times
 
 
 def cuda_timer(fn, reps):

@@ -41,6 +41,7 @@ struct Limits {
 struct Plan {
     std::vector<ImgDesc> d;
     int32_t th = TH_MAX;
+    int32_t hsplit = H_SPLIT_DEFAULT;
     Limits need;
     int32_t n_tiles = 0;
     int64_t n_segs = 0, n_h = 0, n_v = 0, n_p = 0;
@@ -80,6 +81,7 @@ struct ccl_ctx {
     int32_t w = 0, h = 0, pitch = 0;    // fixed shape of a single-image context
     int32_t conn = 0;
     int32_t th = TH_MAX;                // tile height (16 or 32)
+    int32_t hsplit = H_SPLIT_DEFAULT;   // cross-band merge items per boundary word
     Limits cap;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -189,9 +191,10 @@ static ccl_status check_image(const ccl_image_desc &x) {
     return CCL_OK;
 }
 
-static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, Plan *P) {
+static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, int32_t hsplit, Plan *P) {
     P->d.assign(n, ImgDesc{});
     P->th = th;
+    P->hsplit = hsplit;
     int64_t tiles = 0, segs = 0, px = 0, edges = 0, ncap = 0, hi = 0, vi = 0, pi = 0;
     bool any_labels = false;
     for (int i = 0; i < n; ++i) {
@@ -231,7 +234,7 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, Plan *
         px += (int64_t)x.w * x.h;
         edges += 2 * (int64_t)x.w * d.TY + 2 * (int64_t)x.h * d.TX;
         ncap += d.ncap;
-        hi += (int64_t)(d.TY - 1) * d.TX * WPR * H_SPLIT;
+        hi += (int64_t)(d.TY - 1) * d.TX * WPR * hsplit;
         vi += (int64_t)(d.TX - 1) * x.h;
         pi += 2 * (int64_t)d.TX * WPR + 2 * (int64_t)x.h;
     }
@@ -263,6 +266,7 @@ static Batch make_batch(const ccl_ctx *c, const Plan &P) {
     B.n_pitems = P.n_p;
     B.conn = c->conn;
     B.labels = P.labels ? 1 : 0;
+    B.hsplit = P.hsplit;
     B.s = c->s;
     return B;
 }
@@ -302,6 +306,7 @@ static Shape shape_of(const ccl_ctx *c, const Plan &P) {
     Shape s;
     s.v.push_back(c->conn);
     s.v.push_back(P.th);
+    s.v.push_back(P.hsplit);
     for (const ImgDesc &d : P.d) {
         s.v.push_back(d.w);
         s.v.push_back(d.h);
@@ -424,7 +429,7 @@ ccl_status ccl_analyze(ccl_ctx *ctx, const uint8_t *d_img, int32_t *d_fg_labels,
     x.counts = d_counts;
     x.capacity = formula_capacity(ctx->w, ctx->h);
     Plan P;
-    ccl_status st = build_plan(&x, 1, ctx->th, &P);
+    ccl_status st = build_plan(&x, 1, ctx->th, ctx->hsplit, &P);
     if (st != CCL_OK) return st;
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
@@ -539,7 +544,7 @@ ccl_status ccl_create_batched(ccl_ctx **out, int32_t max_images, int64_t max_tot
 ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, int32_t n, ccl_stream_t stream) {
     if (!ctx || !ctx->batched || !host_descs || n <= 0) return CCL_ERR_ARG;
     Plan P;
-    ccl_status st = build_plan(host_descs, n, ctx->th, &P);
+    ccl_status st = build_plan(host_descs, n, ctx->th, ctx->hsplit, &P);
     if (st != CCL_OK) return st;
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
@@ -559,6 +564,13 @@ ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stre
 ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows) {
     if (!ctx || (rows != 16 && rows != 32)) return CCL_ERR_ARG;
     ctx->th = rows;
+    return CCL_OK;
+}
+
+ccl_status ccl_set_merge_split(ccl_ctx *ctx, int32_t items_per_word) {
+    if (!ctx || (items_per_word != 1 && items_per_word != 2 && items_per_word != 4 && items_per_word != 8))
+        return CCL_ERR_ARG;
+    ctx->hsplit = items_per_word;
     return CCL_OK;
 }
 

@@ -29,10 +29,10 @@ constexpr int TH_MIN = 16;             // chosen per context (ccl_set_tile_rows)
 constexpr int TILE_PX = TH_MAX * TW;   // 32768: local pixel index fits 15 bits
 constexpr int NTHREADS = 256;          // threads of the write / resolve / canon kernels
 constexpr int NWARPS = NTHREADS / 32;
-// Horizontal tile-boundary merge items per word of the boundary row (each
-// takes 32 / H_SPLIT of the word's columns, so a dense boundary spreads its
-// unions over more threads).
-constexpr int H_SPLIT = 4;
+// Horizontal tile-boundary merge items per word of the boundary row: each
+// item takes 32 / hsplit of the word's columns, so a dense boundary spreads
+// its unions over more threads (a per-context choice, Batch::hsplit).
+constexpr int H_SPLIT_DEFAULT = 4;
 constexpr int SCAN_B = 256;            // segments per block of the node scan
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -117,6 +117,7 @@ struct Batch {
     int64_t n_hitems, n_vitems, n_pitems;
     int32_t conn;
     int32_t labels;
+    int32_t hsplit;            // cross-band merge items per boundary word: 1, 2, 4 or 8
     Scratch s;
 };
 

@@ -146,7 +146,8 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     B.n_img = 1;
     B.n_tiles = (int32_t)tiles;
     B.n_segs = segs;
-    B.n_hitems = (int64_t)(d.TY - 1) * d.TX * WPR * H_SPLIT;
+    B.hsplit = H_SPLIT_DEFAULT;
+    B.n_hitems = (int64_t)(d.TY - 1) * d.TX * WPR * B.hsplit;
     B.n_vitems = (int64_t)(d.TX - 1) * h;
     B.n_pitems = 2 * (int64_t)d.TX * WPR + 2 * (int64_t)h;
     B.conn = CCL_CONN_8FG_4BG;

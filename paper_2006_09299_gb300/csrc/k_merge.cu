@@ -59,12 +59,13 @@ __device__ __forceinline__ uint32_t starts(uint32_t c, uint32_t cl, int j, uint3
 template <int CONN>
 __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool *ok) {
     const int64_t words = (int64_t)d.TX * WPR;
-    const int part = (int)(item % H_SPLIT);   // columns [part, part + 1) x 32 / H_SPLIT of the word
-    item /= H_SPLIT;
+    const int hs = B.hsplit;
+    const int part = (int)(item % hs);   // columns [part, part + 1) x 32 / hsplit of the word
+    item /= hs;
     const int bb = (int)(item / words);        // boundary between band bb and bb+1
     const int j = (int)(item - (int64_t)bb * words);
-    constexpr int SPAN = 32 / H_SPLIT;
-    const uint32_t range = ((1u << SPAN) - 1u) << (SPAN * part);
+    const int span = 32 / hs;
+    const uint32_t range = span == 32 ? FULL : (((1u << span) - 1u) << (span * part));
     const int x = 32 * j;
     if (x >= d.w) return;
     const int yu = (bb + 1) * B.th - 1, yd = yu + 1;

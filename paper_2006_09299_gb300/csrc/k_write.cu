@@ -305,8 +305,10 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
         };
 
         // ---- node ids of the roots; global records of spilled multi-run roots
+        uint32_t info_nx = tid < n_roots ? ri[tid] : 0u;   // one iteration ahead
         for (int k = tid; k < n_roots; k += NT) {
-            const uint32_t info = ri[k];
+            const uint32_t info = info_nx;
+            if (k + NT < n_roots) info_nx = ri[k + NT];
             const int id = root_id(info);
             if (k < MAXID) sId[k] = id;
             if (k < n_multi && k >= MAXR && !((info >> 17) & 1u) && id < cap) {
@@ -389,12 +391,18 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
         // lanes apart: a segmented scan along such stride-2 chains of equal
         // (root, row) sums them, and only the chain's last lane updates the
         // shared record.
+        // records loaded one iteration ahead (the last lane also the record
+        // after its run's)
+        uint32_t v_nx = tid < n ? rr[tid] : 0xFFFFFFFFu;
+        uint32_t vl_nx = lane == 31 && tid + 1 < n ? rr[tid + 1] : 0xFFFFFFFFu;
         for (int i0 = 0; i0 < n; i0 += NT) {
             const int i = i0 + tid;
-            const uint32_t v = i < n ? rr[i] : 0xFFFFFFFFu;
-            // the next run's start: the next lane's record (the last lane loads it)
+            const uint32_t v = v_nx, vl = vl_nx;
+            if (i + NT < n) v_nx = rr[i + NT];
+            if (lane == 31 && i + NT + 1 < n) vl_nx = rr[i + NT + 1];
+            // the next run's start: the next lane's record
             uint32_t vn = __shfl_down_sync(FULL, v, 1);
-            if (lane == 31) vn = i + 1 < n ? rr[i + 1] : 0xFFFFFFFFu;
+            if (lane == 31) vn = vl;
             const int k = rec_root(v), pix = rec_pix(v), r = pix >> 10, s = pix & (TW - 1);
             const bool multi = i < n && k < n_multi;
             int en = tw;
@@ -456,24 +464,37 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
             const uint32_t nbw = sNB[word];
             uint32_t m = nbw;
             while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const int c = 32 * lane + b;
-                const int id = 1 + sRowSeg[r] + (int)sNBPre[word] + __popc(nbw & mask_lt(b));
-                int p = 0;
-                if (r > 0) {
-                    p = id_of(rec_root(rr[ord_at(r - 1, c)]));
-                } else if (y0 > 0) {
-                    // the bottom edge cell of the tile above, same column
-                    const uint32_t s2b = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
-                    const uint32_t root = (uint32_t)B.s.gp[s2b];
-                    p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
+                // up to two nodes at a time, their lookups in flight together
+                int bb[2], pq[2];
+                uint32_t pv[2] = {0u, 0u};
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    bb[u] = m ? __ffs(m) - 1 : -1;
+                    if (m) m &= m - 1;
+                    pq[u] = bb[u] >= 0 && r > 0 ? ord_at(r - 1, 32 * lane + bb[u]) : -1;
+                    if (pq[u] >= 0) pv[u] = rr[pq[u]];
                 }
-                if (id < cap) {
-                    d.parent[id] = p;
-                    if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[word] >> b) & 1u);
-                } else {
-                    over = true;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int b = bb[u];
+                    if (b < 0) continue;
+                    const int c = 32 * lane + b;
+                    const int id = 1 + sRowSeg[r] + (int)sNBPre[word] + __popc(nbw & mask_lt(b));
+                    int p = 0;
+                    if (r > 0) {
+                        p = id_of(rec_root(pv[u]));
+                    } else if (y0 > 0) {
+                        // the bottom edge cell of the tile above, same column
+                        const uint32_t s2b = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
+                        const uint32_t root = (uint32_t)B.s.gp[s2b];
+                        p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
+                    }
+                    if (id < cap) {
+                        d.parent[id] = p;
+                        if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[word] >> b) & 1u);
+                    } else {
+                        over = true;
+                    }
                 }
             }
         }
@@ -481,9 +502,11 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
 
         // ---- per local root: features (records of multi-run roots; the run
         // itself for a single-run root)
+        uint32_t fin_nx = tid < n_roots ? ri[tid] : 0u;   // one iteration ahead
         for (int k = tid; k < n_roots; k += NT) {
+            const uint32_t info = fin_nx;
+            if (k + NT < n_roots) fin_nx = ri[k + NT];
             if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
-            const uint32_t info = ri[k];
             const int idx = info & 0xFFFF, r = idx >> 10, c = idx & 1023;
             const bool isb = (info >> 17) & 1u;
             const int id = id_of(k);

@@ -8,27 +8,33 @@ from paper_2006_09299_gb300 import autotune, inputs
 class FakeCtx:
     def __init__(self):
         self.rows = None
-        self.calls = []
+        self.split = None
 
     def set_tile_rows(self, rows):
         self.rows = rows
 
+    def set_merge_split(self, split):
+        self.split = split
 
-def test_tune_picks_fastest_and_caches(tmp_path):
+
+def test_tune_picks_fastest_shape_and_schedule_and_caches(tmp_path):
     ctx = FakeCtx()
-    cost = {32: 2.0, 16: 1.5}
-    timer = lambda fn, reps: cost[ctx.rows]
+    cost = {(32, 4): 2.0, (16, 4): 1.5, (16, 1): 1.6, (16, 2): 1.4, (16, 8): 1.45, (32, 1): 0.1, (32, 2): 0.9,
+            (32, 8): 0.8}
+    timer = lambda fn, reps: cost[(ctx.rows, ctx.split)]
     path = str(tmp_path / "t.json")
-    rows, times = autotune.tune(ctx, lambda: None, "k1", cache_path=path, timer=timer)
-    assert rows == 16 and ctx.rows == 16 and times == cost
+    choice, times = autotune.tune(ctx, lambda: None, "k1", cache_path=path, timer=timer)
+    # heights first at the default schedule, then schedules at the best height
+    assert choice == {"rows": 16, "cols": 1024, "merge_split": 2} and (ctx.rows, ctx.split) == (16, 2)
+    assert set(times) == {autotune.choice_name(r, s) for r, s in [(32, 4), (16, 4), (16, 1), (16, 2), (16, 8)]}
     # cached: the timer is not consulted again
     ctx2 = FakeCtx()
-    rows2, _ = autotune.tune(ctx2, lambda: None, "k1", cache_path=path,
-                             timer=lambda fn, reps: pytest.fail("re-timed"))
-    assert rows2 == 16 and ctx2.rows == 16
-    cost[32] = 1.0
-    rows3, _ = autotune.tune(ctx, lambda: None, "k1", cache_path=path, timer=timer, force=True)
-    assert rows3 == 32
+    choice2, _ = autotune.tune(ctx2, lambda: None, "k1", cache_path=path,
+                               timer=lambda fn, reps: pytest.fail("re-timed"))
+    assert choice2 == choice and (ctx2.rows, ctx2.split) == (16, 2)
+    cost[(32, 4)] = 1.0
+    choice3, _ = autotune.tune(ctx, lambda: None, "k1", cache_path=path, timer=timer, force=True)
+    assert choice3 == {"rows": 32, "cols": 1024, "merge_split": 1}
 
 
 def test_size_class_buckets():
@@ -39,8 +45,8 @@ def test_size_class_buckets():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("rows", [16, 32])
-def test_tile_heights_agree_with_oracle(rows):
+@pytest.mark.parametrize("rows,split", [(16, 4), (32, 4), (32, 1), (32, 2), (32, 8), (16, 1), (16, 8)])
+def test_tile_heights_agree_with_oracle(rows, split):
     import torch
 
     import __graft_entry__ as g
@@ -58,6 +64,7 @@ def test_tile_heights_agree_with_oracle(rows):
         for conn in (0, 1):
             ctx = ccl.Context(w, h, pitch, conn=conn)
             ctx.set_tile_rows(rows)
+            ctx.set_merge_split(split)
             out = ctx.analyze(torch.from_numpy(padded).cuda())
             ctx.fill_holes(8)
             n, nf, nb, st = ctx.get_counts()

@@ -33,3 +33,16 @@ def test_recorded_traffic_scales_and_goes_stale(tmp_path, monkeypatch):
     (csrc / "k.cu").write_text("int f(int a) { return -a; }\n")
     assert bench.recorded_traffic("k.cu", "sweep4096", 1000) is None      # code changed since
 
+
+
+def test_source_hash_follows_local_headers(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2006_09299_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (csrc / "dev.cuh").write_text("inline int g(int a) { return a; }\n")
+    (csrc / "k.cu").write_text('#include "dev.cuh"\n#include <cstdint>\nint f(int a) { return g(a); }\n')
+    h0 = bench.kernel_source_hash("k.cu")
+    (csrc / "dev.cuh").write_text("inline int g(int a) { return a; }   // comment only\n")
+    assert bench.kernel_source_hash("k.cu") == h0
+    (csrc / "dev.cuh").write_text("inline int g(int a) { return a + 1; }\n")
+    assert bench.kernel_source_hash("k.cu") != h0          # a header edit makes the record stale

@@ -281,29 +281,36 @@ def test_filter_batched_objects(ccl):
 
 def test_uneven256_full_batch_as_benched(ccl):
     """The full 256-image uneven batch (about 99 Mpx) in one batched call,
-    the launch configuration the bench times (autotuned tile height, CUDA
-    graph replay), every image against the oracle."""
+    the launch configuration the bench times (CUDA graph replay), under every
+    tile height and merge schedule the autotuner can pick, every image
+    against the oracle."""
     batch = inputs.uneven_batch(seed=4, n=256)
     imgs = [(to_dev(p), w) for p, w in batch]
     shapes = [(w, p.shape[0]) for p, w in batch]
     tot = sum(p.shape[0] * w for p, w in batch)
+    refs = []
+    for p, w in batch:
+        r = run_oracle(p, w)
+        f = orc.fill(r, 64)
+        r.pop("node")   # not compared; keeps the host copy of 256 results smaller
+        refs.append((r, f))
     bctx = ccl.BatchContext(len(batch), tot, 2048)
     outs = bctx.new_outputs(shapes, labels=True, fill=True)
-    for rows in (32, 16):
+    # every tile shape and merge schedule the autotuner can choose
+    for rows, split in [(32, 4), (16, 4), (32, 1), (32, 2), (32, 8), (16, 1), (16, 2), (16, 8)]:
         bctx.set_tile_rows(rows)
+        bctx.set_merge_split(split)
         for _ in range(2):   # the second call replays the cached graph
             bctx.analyze(imgs, outs=outs)
             bctx.fill_holes(64)
         torch.cuda.synchronize()
-        for (p, w), o in zip(batch, outs):
-            r = run_oracle(p, w)
+        for o, (r, (fmap, ff, fpar)) in zip(outs, refs):
             n = o.n
-            assert o.status() == 0 and n == r["n"]
+            assert o.status() == 0 and n == r["n"], (rows, split)
             np.testing.assert_array_equal(o.fg.cpu().numpy(), r["fg"])
             np.testing.assert_array_equal(o.bg.cpu().numpy(), r["bg"])
             np.testing.assert_array_equal(o.parent[:n].cpu().numpy(), r["parent"])
             np.testing.assert_array_equal(o.features[:, :n].cpu().numpy(), r["feat"])
-            fmap, ff, fpar = orc.fill(r, 64)
             np.testing.assert_array_equal(o.fill_map[:n].cpu().numpy(), fmap)
             np.testing.assert_array_equal(o.filled_features[:, :n].cpu().numpy(), ff)
             np.testing.assert_array_equal(o.filled_parent[:n].cpu().numpy(), fpar)

@@ -373,9 +373,16 @@ def test_object_removal_matches_brute_force(T):
         assert len(pairs) == len({a for a, _ in pairs}) == len({b for _, b in pairs})
         for a, b in pairs:
             assert list(ff[:, a]) == list(res2["feat"][:, b])
-        # the relabelled images equal the repainted image's labels up to renumbering
+        # the relabelled images equal the repainted image's labels up to
+        # renumbering: colours agree pixel by pixel, and the survivor ids
+        # written in them partition the image exactly as the repainted
+        # image's own labelling does (a bijection between the two id sets)
         fg2, bg2 = orc.relabel(res, fmap)
         assert np.array_equal(fg2 >= 0, painted != 0) and np.array_equal(bg2 >= 0, painted == 0)
+        ids = np.where(fg2 >= 0, fg2, bg2)
+        assert ids.min() >= 0
+        idpairs = set(zip(ids.ravel().tolist(), res2["node"].ravel().tolist()))
+        assert len(idpairs) == len({a for a, _ in idpairs}) == len({b for _, b in idpairs})
         for k in range(res["n"]):
             if fmap[k] != k:
                 assert fpar[k] == -1 and ff[orc.AREA, k] == 0

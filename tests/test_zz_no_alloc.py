@@ -2,7 +2,8 @@
 memory (their memory belongs to another allocator, or they run loops that
 must not call cudaMalloc after start-up). Its scratch is a fixed per-device
 array inside the library; these tests check, through the C ABI, that two
-calls in a row give exactly what the allocating entry point gives, and that
+calls in a row give exactly what the allocating entry point gives and what
+the CPU oracle gives (also at the documented size limits), and that
 oversized images are refused before anything is enqueued.
 
 This file is collected last on purpose, so that a run stopping at the first
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import reference as orc
 from paper_2006_09299_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +61,37 @@ def test_static_matches_allocating_entry_point_twice(ccl):
             assert torch.equal(out.bg.cpu(), ref[1]), call
             assert torch.equal(out.parent[:n].cpu(), ref[2]), call
             assert torch.equal(out.features[:, :n].cpu(), ref[3]), call
+
+
+@pytest.mark.parametrize("w,h,d,g", [
+    (1024, 1024, 0.5, 1),    # exactly 2^20 pixels
+    (4096, 256, 0.45, 2),    # the widest side allowed, four tile columns
+    (256, 4096, 0.5, 3),     # the tallest side allowed
+    (1, 4096, 0.5, 1),       # one pixel wide
+    (1023, 1025, 0.4, 1),    # w not a multiple of 4: scalar label stores
+])
+def test_static_at_its_limits_matches_the_oracle_twice(ccl, w, h, d, g):
+    """Images at the documented size limits, against the CPU oracle itself
+    (labels, tree, features, counts), on two calls in a row."""
+    img = inputs.granular(h, w, d, g, 1000 + w + h)
+    pitch = -(-w // 16) * 16
+    padded = inputs.pitched(img, pitch)
+    ref = orc.analyze(padded, w=w)
+    dev = torch.from_numpy(padded).cuda()
+    out = ccl.Analysis(w, h, ccl.node_capacity(w, h), True, "cuda")
+    for call in range(2):
+        out.fg.fill_(-7)
+        out.bg.fill_(-7)
+        ccl.analyze_static(dev, w, out)
+        torch.cuda.synchronize()
+        n = out.n
+        assert out.status() == 0, call
+        assert n == ref["n"], call
+        assert out.counts[:3].cpu().tolist() == ref["counts"][:3].tolist(), call
+        np.testing.assert_array_equal(out.fg.cpu().numpy(), ref["fg"])
+        np.testing.assert_array_equal(out.bg.cpu().numpy(), ref["bg"])
+        np.testing.assert_array_equal(out.parent[:n].cpu().numpy(), ref["parent"])
+        np.testing.assert_array_equal(out.features[:, :n].cpu().numpy(), ref["feat"])
 
 
 def test_static_refuses_oversized_images(ccl):
