@@ -305,6 +305,8 @@ def run_ours(args, rank, world, local_rank):
         extra["rings8192"] = single_image_record(ccl, dev, stream, inputs.rings(), 8192, args.steps, args.warmup,
                                                  "rings8192", cpu=world == 1 and not args.no_cpu_baseline)
         extra["latency_512"] = latency_512(ccl, dev, stream)
+        if not args.no_serve and world == 1:
+            extra["serve"] = serve_sweep(args, confirm_s=args.serve_seconds)
 
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gpixel/s", "n_gpus": world,
@@ -759,65 +761,93 @@ def run_reference(args, rank, world):
     }
 
 
-def run_serve(args):
-    """Serving stream: Poisson arrivals of mixed-size frames through the
-    continuous-batching server; sweep the arrival rate, report p50/p99 latency
-    and throughput at the highest rate whose queue stays bounded."""
+def serve_sweep(args, rates=None, confirm_s=10.0, search_s=2.0):
+    """Serving stream: Poisson arrivals of mixed-size blob frames through the
+    continuous-batching server. The sustained rate follows the rule: a rate
+    is sustained when, over a confirm_s-second window of arrivals, the queue
+    stays bounded (its depth never trends up: at most 4 batches waiting in
+    95 % of the samples and at most 2 at the end) and every request
+    completes. A short search (search_s seconds per rate) finds the highest
+    candidate; candidates are then confirmed over confirm_s seconds, highest
+    first. p50 / p99 latency (arrival to result event) are those of the
+    confirmed run."""
+    import gc
     import torch
-    import __graft_entry__ as ge
-    ge.build()
     from paper_2006_09299_gb300 import inputs
     from paper_2006_09299_gb300.serve import GpuBackend, Server, latency_stats, poisson_run
     frames = inputs.frame_stream(seed=5, n=48)
     mean_px = float(np.mean([f.size for f in frames]))
     be = GpuBackend(n_streams=args.serve_streams, max_batch=args.serve_batch)
     # one server for the whole sweep: its resident slots (device buffers and
-    # pinned staging) are allocated during a short warm-up and then reused
+    # pinned staging) are allocated up front and then reused
     srv = Server(be, memory_budget=16 << 30, max_batch=args.serve_batch, n_streams=args.serve_streams)
-    import gc
     srv.start()
-    rows = []
-    best = None
-    # resident slots for every frame size: enough for a full batch on every
-    # stream plus the one being admitted
     srv.preallocate(sorted({be.size_key(f) for f in frames}), args.serve_batch * (args.serve_streams + 1))
-    gc.collect()
-    gc.disable()   # no collector pauses inside the latency measurement
-    try:
-        poisson_run(srv, frames, 1000, 1.0, seed=1)
-        for rate in [int(x) for x in args.serve_rates.split(",")]:
-            ticks0 = srv.ticks
-            reqs, depth = poisson_run(srv, frames, rate, args.serve_seconds, seed=rate)
-            rows.append((rate, reqs, depth, srv.ticks - ticks0))
-    finally:
-        srv.stop()
-        gc.enable()
-    results, rows = rows, []
-    for rate, reqs, depth, ticks in results:
+    rates = rates or [int(x) for x in args.serve_rates.split(",")]
+    bound = 4 * args.serve_batch
+
+    def one(rate, seconds):
+        ticks0 = srv.ticks
+        reqs, depth, samples = poisson_run(srv, frames, rate, seconds, seed=rate, depth_samples=True)
         st = latency_stats(reqs)
         done = [r for r in reqs if r.t_done is not None]
         span = (max(r.t_done for r in done) - min(r.t_arrive for r in done)) if done else 1.0
         px = sum(r.pixels for r in done)
-        row = dict(rate_hz=rate, frames=len(reqs), queue_at_end=depth, gpx_s=round(px / span / 1e9, 3),
-                   ticks=ticks, **st)
-        row["sustained"] = depth <= 2 * args.serve_batch and len(done) == len(reqs)
-        rows.append(row)
+        q95 = sorted(samples)[int(0.95 * (len(samples) - 1))] if samples else 0
+        row = dict(rate_hz=rate, seconds=seconds, frames=len(reqs), queue_at_end=depth, queue_p95=q95,
+                   queue_max=max(samples) if samples else 0, gpx_s=round(px / span / 1e9, 3),
+                   ticks=srv.ticks - ticks0, **st)
+        row["sustained"] = depth <= 2 * args.serve_batch and q95 <= bound and len(done) == len(reqs)
         log("serve", row)
-        # the maximum sustained rate: every rate up to it kept its queue bounded
-        if row["sustained"] and all(x["sustained"] for x in rows):
-            best = row
+        return row
+
+    gc.collect()
+    gc.disable()   # no collector pauses inside the latency measurement
+    search, confirmed = [], []
+    try:
+        poisson_run(srv, frames, 1000, 1.0, seed=1)   # warm-up
+        for rate in rates:
+            row = one(rate, search_s)
+            search.append(row)
+            if not row["sustained"]:
+                break
+        cands = [r["rate_hz"] for r in search if r["sustained"]][::-1][:3]
+        for rate in cands:
+            row = one(rate, confirm_s)
+            confirmed.append(row)
+            if row["sustained"]:
+                break
+    finally:
+        srv.stop()
+        gc.enable()
     torch.cuda.synchronize()
-    b = best or rows[0]
+    best = next((r for r in confirmed if r["sustained"]), None)
+    b = best or (confirmed[-1] if confirmed else search[0])
     return {
-        "metric": METRIC, "value": b["gpx_s"], "unit": "Gpixel/s", "n_gpus": 1, "steps": len(rows),
-        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic (seeded generators shaped like the paper's workloads)",
-        "config": {"workload": "serving stream: Poisson arrivals of blob frames from {640x480, 1920x1080, 3840x2160}, "
-                               "continuous batching, memory-admitted, fill 64",
-                   "mean_frame_px": mean_px, "max_batch": args.serve_batch, "streams": args.serve_streams,
-                   "seconds_per_rate": args.serve_seconds},
-        "serving": {"max_sustained_rate_hz": b["rate_hz"] if best else None, "p50_ms": b["p50_ms"],
-                    "p99_ms": b["p99_ms"], "sweep": rows},
+        "workload": "serving stream: Poisson arrivals of blob frames from {640x480, 1920x1080, 3840x2160}, "
+                    "continuous batching, memory-admitted, fill 64",
+        "mean_frame_px": mean_px, "max_batch": args.serve_batch, "streams": args.serve_streams,
+        "rule": "sustained = over %.0f s of arrivals the queue stays bounded (95th-percentile depth <= %d, "
+                "depth at the end <= %d) and every request completes" % (confirm_s, bound, 2 * args.serve_batch),
+        "max_sustained_rate_hz": best["rate_hz"] if best else None,
+        "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "gpx_s": b["gpx_s"],
+        "search": search, "confirm": confirmed,
+    }
+
+
+def run_serve(args):
+    """bench.py --workload serve: the serving sweep alone, as one JSON line."""
+    import __graft_entry__ as ge
+    ge.build()
+    rec = serve_sweep(args, confirm_s=args.serve_seconds)
+    return {
+        "metric": METRIC, "value": rec["gpx_s"], "unit": "Gpixel/s", "n_gpus": 1,
+        "steps": len(rec["search"]) + len(rec["confirm"]), "warmup": 0, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded generators shaped like the paper's workloads)",
+        "config": {"workload": rec["workload"], "mean_frame_px": rec["mean_frame_px"], "max_batch": rec["max_batch"],
+                   "streams": rec["streams"], "confirm_seconds": args.serve_seconds},
+        "serving": rec,
     }
 
 
@@ -968,8 +998,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep4096", choices=["sweep4096", "rings8192", "uneven256", "serve", "paper2048"])
     ap.add_argument("--paper-per-cell", type=int, default=4, help="paper2048: images per density x granularity cell")
-    ap.add_argument("--serve-rates", default="500,1000,2000,4000,6000,8000,10000,12000,16000")
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-rates", default="2000,4000,6000,8000,10000,12000,16000")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="confirmation window per rate")
+    ap.add_argument("--no-serve", action="store_true", help="default line: leave out the serving record")
     ap.add_argument("--serve-batch", type=int, default=16)
     ap.add_argument("--serve-streams", type=int, default=2)
     ap.add_argument("--no-extra", action="store_true")

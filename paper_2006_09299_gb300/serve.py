@@ -362,15 +362,17 @@ class GpuBackend:
 # ----------------------------------------------------------------- driver
 
 
-def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True, drain_s=30.0):
+def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True, drain_s=30.0, depth_samples=False):
     """Submit frames (cycled) with Poisson arrivals at rate_hz for duration_s;
     wait (at most drain_s in all) for the admitted work to finish. Returns the
-    requests and the queue depth seen at the end of the arrival window;
-    raises if the scheduler failed."""
+    requests and the queue depth seen at the end of the arrival window (and,
+    with depth_samples, the queue depth sampled at every arrival); raises if
+    the scheduler failed."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     t_next = t0
     reqs = []
+    samples = []
     unreleased = collections.deque()
     i = 0
     while True:
@@ -384,6 +386,8 @@ def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True, drain
             raise RuntimeError("the serving scheduler failed") from server.error
         reqs.append(server.submit(frames[i % len(frames)], t_arrive=t_next))
         unreleased.append(reqs[-1])
+        if depth_samples:
+            samples.append(len(server.waiting) + len(server.admitted))
         i += 1
         # hand back the slots of finished requests (their results were
         # consumed), oldest first: requests finish roughly in arrival order
@@ -400,7 +404,7 @@ def poisson_run(server, frames, rate_hz, duration_s, seed=0, release=True, drain
             server.release(r)
     if server.error is not None:
         raise RuntimeError("the serving scheduler failed") from server.error
-    return reqs, depth_end
+    return (reqs, depth_end, samples) if depth_samples else (reqs, depth_end)
 
 
 def latency_stats(reqs):

@@ -113,6 +113,19 @@ def test_cancel_before_launch():
     assert [rid for _, b in be.launches for rid in b] == [r1.rid]
 
 
+def test_poisson_driver_samples_the_queue_depth():
+    be = FakeBackend(delay=0.001)
+    s = Server(be, memory_budget=10**9, max_batch=8, n_streams=2)
+    s.start()
+    try:
+        reqs, depth, samples = poisson_run(s, [np.zeros((3, 3), np.uint8)], rate_hz=1000, duration_s=0.2,
+                                           depth_samples=True)
+    finally:
+        s.stop()
+    assert len(samples) == len(reqs) > 50 and min(samples) >= 0 and depth >= 0
+    assert sorted(samples)[int(0.95 * (len(samples) - 1))] <= 4 * 8   # a fast backend keeps the queue short
+
+
 def test_poisson_driver_and_latency_stats():
     be = FakeBackend(delay=0.001)
     s = Server(be, memory_budget=10**9, max_batch=8, n_streams=2)
