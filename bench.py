@@ -348,7 +348,8 @@ def pick_tile_rows(args, ctx, step, shapes):
     from paper_2006_09299_gb300 import autotune
     if args.tile_rows != "auto":
         ctx.set_tile_rows(int(args.tile_rows))
-        return {"rows": int(args.tile_rows), "cols": autotune.TILE_COLS,
+        ctx.set_tile_cols(int(args.tile_cols))
+        return {"rows": int(args.tile_rows), "cols": int(args.tile_cols),
                 "merge_split": autotune.MERGE_SPLITS[0], "chosen_by": "flag"}
     path = os.path.join(tempfile.mkdtemp(), "tune.json")
     choice, times = autotune.tune(ctx, step, autotune.size_class(shapes), cache_path=path, reps=3, warmup=2)
@@ -1010,6 +1011,7 @@ def main():
     ap.add_argument("--tight", action="store_true", help="node arrays sized w*h/4 instead of the bound")
     ap.add_argument("--pick", default="", help="comma-separated image indices of the workload to use")
     ap.add_argument("--tile-rows", default="auto", choices=["auto", "16", "32"])
+    ap.add_argument("--tile-cols", default="1024", choices=["512", "1024"], help="with a fixed --tile-rows")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = dist_env()

@@ -221,10 +221,17 @@ ccl_status ccl_filter_components_batched(ccl_ctx *ctx, int32_t target, int64_t a
 ccl_status ccl_relabel_filtered_batched(ccl_ctx *ctx, int32_t *const *d_fg_out, int32_t *const *d_bg_out,
                                         ccl_stream_t stream);
 
-/* Tile height for later analyses of this context: 32 rows (default) or 16
- * rows of 1024 columns. Results are identical; the speed differs with the
- * image (ccl.autotune picks one per size class by timing both). */
+/* Tile height for later analyses of this context: 32 rows (default) or 16.
+ * Results are identical; the speed differs with the image (ccl.autotune
+ * picks one per size class by timing the choices). */
 ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows);
+
+/* Tile width for later analyses of this context: 1024 columns (default, one
+ * 32-pixel word per thread of a tile row's warp) or 512. Narrower tiles give
+ * small or narrow images more tiles to spread over the SMs; wider tiles have
+ * fewer tile edges to merge. Results are identical; ccl.autotune times the
+ * choices. Other values: CCL_ERR_ARG. */
+ccl_status ccl_set_tile_cols(ccl_ctx *ctx, int32_t cols);
 
 /* Merge schedule for later analyses of this context: the number of work
  * items that share one 32-pixel word of a boundary between two bands of

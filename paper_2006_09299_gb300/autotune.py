@@ -1,24 +1,27 @@
 """Autotuner for the tile shape and merge schedule of the CUDA path.
 
-Two launch choices change the speed but never the results:
-  - the tile height, 32 or 16 rows of 1024 columns (ccl_set_tile_rows):
-    taller tiles have fewer tile edges to merge across, shorter tiles let
-    more CTAs share an SM and hide more latency;
+Three launch choices change the speed but never the results:
+  - the tile height, 32 or 16 rows (ccl_set_tile_rows): taller tiles have
+    fewer tile edges to merge across, shorter tiles let more CTAs share an
+    SM and hide more latency;
+  - the tile width, 1024 or 512 columns (ccl_set_tile_cols): narrower tiles
+    give small or narrow images more tiles to spread over the SMs, wider
+    tiles fewer vertical tile edges;
   - the merge schedule, 1, 2, 4 or 8 work items per 32-pixel word of a
     boundary between bands of tiles (ccl_set_merge_split): more items spread
     a dense boundary's unions over more threads, fewer cost less on sparse
     boundaries.
 Which wins depends on the images, so the tuner times the caller's own work
-with CUDA events: first every tile height at the default merge schedule,
-then every merge schedule at the best height, and keeps the fastest pair
-per size class in a small JSON cache.
+with CUDA events: first every tile shape (height x width) at the default
+merge schedule, then every merge schedule at the best shape, and keeps the
+fastest choice per size class in a small JSON cache.
 """
 import json
 import os
 
 TILE_ROWS = (32, 16)
+TILE_COLS = (1024, 512)
 MERGE_SPLITS = (4, 1, 2, 8)      # the first is the default
-TILE_COLS = 1024
 
 
 def size_class(shapes, n_images=None):
@@ -58,12 +61,14 @@ def _store(path, data):
     os.replace(tmp, path)
 
 
-def choice_name(rows, split):
-    return "rows%d_cols%d_split%d" % (rows, TILE_COLS, split)
+def choice_name(rows, cols, split):
+    return "rows%d_cols%d_split%d" % (rows, cols, split)
 
 
 def apply(ctx, choice):
     ctx.set_tile_rows(choice["rows"])
+    if hasattr(ctx, "set_tile_cols"):
+        ctx.set_tile_cols(choice["cols"])
     if hasattr(ctx, "set_merge_split"):
         ctx.set_merge_split(choice["merge_split"])
 
@@ -78,30 +83,32 @@ def tune(ctx, run, key, cache_path=None, reps=5, warmup=2, timer=None, force=Fal
     stream. A cached choice for `key` is reused unless force is set."""
     path = cache_path or default_cache_path()
     data = _load(path)
-    if not force and key in data and "merge_split" in data[key]:
-        choice = {"rows": int(data[key]["rows"]), "cols": TILE_COLS, "merge_split": int(data[key]["merge_split"])}
+    if not force and key in data and "merge_split" in data[key] and "cols" in data[key]:
+        choice = {k: int(data[key][k]) for k in ("rows", "cols", "merge_split")}
         apply(ctx, choice)
         return choice, data[key].get("ms", {})
     if timer is None:
         timer = cuda_timer
     times = {}
 
-    def measure(rows, split):
-        c = {"rows": rows, "cols": TILE_COLS, "merge_split": split}
-        apply(ctx, c)
-        for _ in range(warmup):
-            run()
-        times[choice_name(rows, split)] = timer(run, reps)
-        return times[choice_name(rows, split)]
+    def measure(rows, cols, split):
+        name = choice_name(rows, cols, split)
+        if name not in times:
+            apply(ctx, {"rows": rows, "cols": cols, "merge_split": split})
+            for _ in range(warmup):
+                run()
+            times[name] = timer(run, reps)
+        return times[name]
 
     split0 = MERGE_SPLITS[0]
-    best_rows = min(TILE_ROWS, key=lambda r: measure(r, split0))
-    splits = [split0] + [s for s in MERGE_SPLITS[1:] if hasattr(ctx, "set_merge_split")]
-    best_split = min(splits, key=lambda s: times.get(choice_name(best_rows, s)) or measure(best_rows, s))
-    choice = {"rows": best_rows, "cols": TILE_COLS, "merge_split": best_split}
+    cols_choices = TILE_COLS if hasattr(ctx, "set_tile_cols") else TILE_COLS[:1]
+    shapes = [(r, c) for c in cols_choices for r in TILE_ROWS]
+    best_rows, best_cols = min(shapes, key=lambda rc: measure(rc[0], rc[1], split0))
+    splits = MERGE_SPLITS if hasattr(ctx, "set_merge_split") else MERGE_SPLITS[:1]
+    best_split = min(splits, key=lambda sp: measure(best_rows, best_cols, sp))
+    choice = {"rows": best_rows, "cols": best_cols, "merge_split": best_split}
     apply(ctx, choice)
-    data[key] = {"rows": best_rows, "cols": TILE_COLS, "merge_split": best_split,
-                 "ms": {k: round(v, 4) for k, v in times.items()}}
+    data[key] = dict(choice, ms={k: round(v, 4) for k, v in times.items()})
     _store(path, data)
     return choice, times
 

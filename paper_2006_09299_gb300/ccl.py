@@ -56,6 +56,7 @@ SIGNATURES = {
     "ccl_set_graph_cache": (ctypes.c_int, [_p, _i32]),
     "ccl_set_tile_rows": (ctypes.c_int, [_p, _i32]),
     "ccl_set_merge_split": (ctypes.c_int, [_p, _i32]),
+    "ccl_set_tile_cols": (ctypes.c_int, [_p, _i32]),
     "ccl_enable_phase_timing": (ctypes.c_int, [_p, _i32]),
     "ccl_read_phase_timing": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "ccl_get_launch_count": (ctypes.c_int, [_p, ctypes.POINTER(_i64)]),
@@ -124,6 +125,10 @@ class _Instrumented:
     def set_tile_rows(self, rows):
         _check(_lib.ccl_set_tile_rows(self._h, int(rows)), "ccl_set_tile_rows")
         self.tile_rows = int(rows)
+
+    def set_tile_cols(self, cols):
+        _check(_lib.ccl_set_tile_cols(self._h, int(cols)), "ccl_set_tile_cols")
+        self.tile_cols = int(cols)
 
     def set_merge_split(self, items_per_word):
         _check(_lib.ccl_set_merge_split(self._h, int(items_per_word)), "ccl_set_merge_split")

@@ -31,16 +31,17 @@ int64_t formula_capacity(int64_t w, int64_t h) {
 
 // Sizes that a context's scratch must hold.
 struct Limits {
-    int64_t images = 0, tiles = 0, segs = 0, pixels = 0, edges = 0, ncap = 0;
+    int64_t images = 0, tiles = 0, segs = 0, words = 0, pixels = 0, edges = 0, ncap = 0;
     bool fits(const Limits &o) const {
-        return o.images <= images && o.tiles <= tiles && o.segs <= segs && o.pixels <= pixels &&
-               o.edges <= edges && o.ncap <= ncap;
+        return o.images <= images && o.tiles <= tiles && o.segs <= segs && o.words <= words &&
+               o.pixels <= pixels && o.edges <= edges && o.ncap <= ncap;
     }
 };
 
 struct Plan {
     std::vector<ImgDesc> d;
     int32_t th = TH_MAX;
+    int32_t tw = TW_MAX;
     int32_t hsplit = H_SPLIT_DEFAULT;
     Limits need;
     int32_t n_tiles = 0;
@@ -81,6 +82,7 @@ struct ccl_ctx {
     int32_t w = 0, h = 0, pitch = 0;    // fixed shape of a single-image context
     int32_t conn = 0;
     int32_t th = TH_MAX;                // tile height (16 or 32)
+    int32_t tw = TW_MAX;                // tile width (512 or 1024)
     int32_t hsplit = H_SPLIT_DEFAULT;   // cross-band merge items per boundary word
     Limits cap;
     void *scratch = nullptr;
@@ -117,12 +119,14 @@ static Limits limits_of_bounds(int64_t images, int64_t pixels, int64_t max_side)
     L.images = images;
     L.pixels = pixels;
     // tiles of one image <= (h/TH + 1)(w/TW + 1) <= wh/(TH TW) + h/TH + w/TW + 1,
-    // sized for the smaller tile height so that both can run
-    L.tiles = pixels / (TH_MIN * TW) + images * (max_side / TH_MIN + max_side / TW + 1);
+    // sized for the smallest tile so that every tile shape can run
+    L.tiles = pixels / (TH_MIN * TW_MIN) + images * (max_side / TH_MIN + max_side / TW_MIN + 1);
     // tile rows (segments) = h * ceil(w/TW) <= wh/TW + h
-    L.segs = pixels / TW + images * max_side;
+    L.segs = pixels / TW_MIN + images * max_side;
+    // bit-plane words = h * ceil(w/TW) * TW/32 <= wh/32 + h * TW_MAX/32
+    L.words = pixels / 32 + images * max_side * WPR_MAX;
     // edge cells = 2 w TY + 2 h TX <= 2wh/TH + 2w + 2wh/TW + 2h
-    L.edges = 2 * pixels / TH_MIN + 2 * pixels / TW + images * 4 * max_side;
+    L.edges = 2 * pixels / TH_MIN + 2 * pixels / TW_MIN + images * 4 * max_side;
     L.ncap = (3 * pixels) / 4 + images * (max_side / 2 + 3);
     return L;
 }
@@ -134,9 +138,8 @@ static size_t carve(const Limits &L, Scratch *s, ImgDesc **desc, char *base) {
         off += align_up(bytes);
         return p;
     };
-    const int64_t words = L.segs * WPR;
-    s->fgbits = (uint32_t *)take(words * 4);
-    s->nodebits = (uint32_t *)take(words * 4);
+    s->fgbits = (uint32_t *)take(L.words * 4);
+    s->nodebits = (uint32_t *)take(L.words * 4);
     s->run_root = (uint32_t *)take(L.pixels * 4);
     s->rootinfo = (uint32_t *)take(L.pixels * 4);
     s->tstat = (int4 *)take(L.tiles * 16);
@@ -191,10 +194,12 @@ static ccl_status check_image(const ccl_image_desc &x) {
     return CCL_OK;
 }
 
-static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, int32_t hsplit, Plan *P) {
+static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, int32_t tw, int32_t hsplit, Plan *P) {
     P->d.assign(n, ImgDesc{});
     P->th = th;
+    P->tw = tw;
     P->hsplit = hsplit;
+    const int32_t wpr = tw / 32;
     int64_t tiles = 0, segs = 0, px = 0, edges = 0, ncap = 0, hi = 0, vi = 0, pi = 0;
     bool any_labels = false;
     for (int i = 0; i < n; ++i) {
@@ -215,7 +220,7 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, int32_
         d.w = x.w;
         d.h = x.h;
         d.pitch = x.pitch;
-        d.TX = (x.w + TW - 1) / TW;
+        d.TX = (x.w + tw - 1) / tw;
         d.TY = (x.h + th - 1) / th;
         d.tile0 = (int32_t)tiles;
         d.seg0 = segs;
@@ -234,9 +239,9 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, int32_
         px += (int64_t)x.w * x.h;
         edges += 2 * (int64_t)x.w * d.TY + 2 * (int64_t)x.h * d.TX;
         ncap += d.ncap;
-        hi += (int64_t)(d.TY - 1) * d.TX * WPR * hsplit;
+        hi += (int64_t)(d.TY - 1) * d.TX * wpr * hsplit;
         vi += (int64_t)(d.TX - 1) * x.h;
-        pi += 2 * (int64_t)d.TX * WPR + 2 * (int64_t)x.h;
+        pi += 2 * (int64_t)d.TX * wpr + 2 * (int64_t)x.h;
     }
     if (tiles >= INT32_MAX || n + edges >= INT32_MAX) return CCL_ERR_CAPACITY;
     P->n_tiles = (int32_t)tiles;
@@ -248,6 +253,7 @@ static ccl_status build_plan(const ccl_image_desc *in, int n, int32_t th, int32_
     P->need.images = n;
     P->need.tiles = tiles;
     P->need.segs = segs;
+    P->need.words = segs * wpr;
     P->need.pixels = px;
     P->need.edges = edges;
     P->need.ncap = ncap;
@@ -258,6 +264,9 @@ static Batch make_batch(const ccl_ctx *c, const Plan &P) {
     Batch B;
     B.desc = c->d_desc;
     B.th = P.th;
+    B.tw = P.tw;
+    B.wpr = P.tw / 32;
+    B.log_tw = P.tw == 1024 ? 10 : 9;
     B.n_img = (int32_t)P.d.size();
     B.n_tiles = P.n_tiles;
     B.n_segs = P.n_segs;
@@ -306,6 +315,7 @@ static Shape shape_of(const ccl_ctx *c, const Plan &P) {
     Shape s;
     s.v.push_back(c->conn);
     s.v.push_back(P.th);
+    s.v.push_back(P.tw);
     s.v.push_back(P.hsplit);
     for (const ImgDesc &d : P.d) {
         s.v.push_back(d.w);
@@ -389,13 +399,14 @@ ccl_status ccl_create(ccl_ctx **out, int32_t w, int32_t h, int32_t pitch) {
     c->w = w;
     c->h = h;
     c->pitch = pitch;
-    // sized for the smaller tile height (more tiles and edge cells) so that
-    // both tile heights can run
-    const int64_t TX = (w + TW - 1) / TW, TY = (h + TH_MIN - 1) / TH_MIN;
+    // sized for the smallest tile (most tiles, segments and edge cells) so
+    // that every tile shape can run; the widest tile has the most plane words
+    const int64_t TX = (w + TW_MIN - 1) / TW_MIN, TY = (h + TH_MIN - 1) / TH_MIN;
     Limits L;
     L.images = 1;
     L.tiles = TX * TY;
     L.segs = (int64_t)h * TX;
+    L.words = (int64_t)h * ((w + TW_MAX - 1) / TW_MAX) * WPR_MAX;
     L.pixels = (int64_t)w * h;
     L.edges = 2 * (int64_t)w * TY + 2 * (int64_t)h * TX;
     L.ncap = formula_capacity(w, h);
@@ -429,7 +440,7 @@ ccl_status ccl_analyze(ccl_ctx *ctx, const uint8_t *d_img, int32_t *d_fg_labels,
     x.counts = d_counts;
     x.capacity = formula_capacity(ctx->w, ctx->h);
     Plan P;
-    ccl_status st = build_plan(&x, 1, ctx->th, ctx->hsplit, &P);
+    ccl_status st = build_plan(&x, 1, ctx->th, ctx->tw, ctx->hsplit, &P);
     if (st != CCL_OK) return st;
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
@@ -544,7 +555,7 @@ ccl_status ccl_create_batched(ccl_ctx **out, int32_t max_images, int64_t max_tot
 ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, int32_t n, ccl_stream_t stream) {
     if (!ctx || !ctx->batched || !host_descs || n <= 0) return CCL_ERR_ARG;
     Plan P;
-    ccl_status st = build_plan(host_descs, n, ctx->th, ctx->hsplit, &P);
+    ccl_status st = build_plan(host_descs, n, ctx->th, ctx->tw, ctx->hsplit, &P);
     if (st != CCL_OK) return st;
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
@@ -564,6 +575,12 @@ ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stre
 ccl_status ccl_set_tile_rows(ccl_ctx *ctx, int32_t rows) {
     if (!ctx || (rows != 16 && rows != 32)) return CCL_ERR_ARG;
     ctx->th = rows;
+    return CCL_OK;
+}
+
+ccl_status ccl_set_tile_cols(ccl_ctx *ctx, int32_t cols) {
+    if (!ctx || (cols != TW_MIN && cols != TW_MAX)) return CCL_ERR_ARG;
+    ctx->tw = cols;
     return CCL_OK;
 }
 

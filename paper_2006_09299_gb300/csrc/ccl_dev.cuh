@@ -22,11 +22,12 @@
 
 namespace ccl {
 
-constexpr int TW = 1024;               // tile width in pixels (32 words)
-constexpr int WPR = TW / 32;           // 32-bit words per tile row = lanes
+constexpr int TW_MAX = 1024;           // tile width in pixels: 1024 (default, 32 words) or
+constexpr int TW_MIN = 512;            // 512 (16 words), chosen per context (ccl_set_tile_cols)
 constexpr int TH_MAX = 32;             // tile height in rows: 32 (default) or 16,
 constexpr int TH_MIN = 16;             // chosen per context (ccl_set_tile_rows)
-constexpr int TILE_PX = TH_MAX * TW;   // 32768: local pixel index fits 15 bits
+constexpr int TILE_PX = TH_MAX * TW_MAX;   // 32768: local pixel index fits 15 bits
+constexpr int WPR_MAX = TW_MAX / 32;   // most 32-bit words per tile row
 constexpr int NTHREADS = 256;          // threads of the write / resolve / canon kernels
 constexpr int NWARPS = NTHREADS / 32;
 // Horizontal tile-boundary merge items per word of the boundary row: each
@@ -111,6 +112,9 @@ struct Scratch {
 struct Batch {
     const ImgDesc *desc;
     int32_t th;                // tile height of this call (16 or 32)
+    int32_t tw;                // tile width of this call (512 or 1024)
+    int32_t wpr;               // tw / 32: words per tile row
+    int32_t log_tw;            // log2(tw)
     int32_t n_img;
     int32_t n_tiles;
     int64_t n_segs;
@@ -238,7 +242,8 @@ __device__ __forceinline__ void set_status(const Batch &B, const ImgDesc &d, int
 // Geometry of one tile. Per-tile tables are packed without gaps:
 //   px  first entry of the tile's run / root tables (th * tw entries: a tile
 //       has at most one run and one root per pixel), in raster order of
-//       tiles: all bands above hold TH * w pixels, tiles to the left th * TW;
+//       tiles: all bands above hold TH * w pixels, tiles to the left th * TW
+//       (TH, TW: the call's tile height and width);
 //   b   first entry of the tile's edge-cell tables (2 tw + 2 th entries: top
 //       row, bottom row, left column, right column); border roots of the
 //       tile occupy device-wide union-find slots n_img + b + ordinal.
@@ -247,7 +252,7 @@ struct TileGeo {
     int64_t px, b;
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const ImgDesc &d, int lt, int TH) {
+__device__ __forceinline__ TileGeo tile_geo(const ImgDesc &d, int lt, int TH, int TW) {
     TileGeo g;
     g.ty = lt / d.TX;
     g.tx = lt - g.ty * d.TX;

@@ -98,7 +98,7 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     d.w = w;
     d.h = h;
     d.pitch = pitch;
-    d.TX = (w + TW - 1) / TW;
+    d.TX = (w + TW_MAX - 1) / TW_MAX;
     d.TY = (h + TH_MAX - 1) / TH_MAX;
     const int64_t full = ((int64_t)(h + 1) / 2) * ((w + 1) / 2) + ((int64_t)w * h + 1) / 2 + 1;
     d.ncap = capacity < full ? capacity : full;
@@ -117,8 +117,8 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     Scratch s;
     const size_t desc_off = off;
     take(sizeof(ImgDesc));
-    s.fgbits = (uint32_t *)take(segs * WPR * 4);
-    s.nodebits = (uint32_t *)take(segs * WPR * 4);
+    s.fgbits = (uint32_t *)take(segs * WPR_MAX * 4);
+    s.nodebits = (uint32_t *)take(segs * WPR_MAX * 4);
     s.run_root = (uint32_t *)take(px * 4);
     s.rootinfo = (uint32_t *)take(px * 4);
     s.tstat = (int4 *)take(tiles * 16);
@@ -143,13 +143,16 @@ extern "C" ccl_status ccl_analyze_static(const uint8_t *d_img, int32_t w, int32_
     Batch B;
     B.desc = (const ImgDesc *)(p + desc_off);
     B.th = TH_MAX;
+    B.tw = TW_MAX;
+    B.wpr = WPR_MAX;
+    B.log_tw = 10;
     B.n_img = 1;
     B.n_tiles = (int32_t)tiles;
     B.n_segs = segs;
     B.hsplit = H_SPLIT_DEFAULT;
-    B.n_hitems = (int64_t)(d.TY - 1) * d.TX * WPR * B.hsplit;
+    B.n_hitems = (int64_t)(d.TY - 1) * d.TX * WPR_MAX * B.hsplit;
     B.n_vitems = (int64_t)(d.TX - 1) * h;
-    B.n_pitems = 2 * (int64_t)d.TX * WPR + 2 * (int64_t)h;
+    B.n_pitems = 2 * (int64_t)d.TX * WPR_MAX + 2 * (int64_t)h;
     B.conn = CCL_CONN_8FG_4BG;
     B.labels = d_fg_labels != nullptr;
     B.s = s;

@@ -2,7 +2,8 @@
 //
 // The paper's steps 1a and 1b (Algorithms 1 and 2) scan one row at a time and
 // grow one equivalence table for the whole image. Here every tile of 32 rows
-// x 1024 columns (or 16 rows) is handled by one CTA, all rows at once:
+// x 1024 columns (or 16 rows, or 512 columns) is handled by one CTA, all rows
+// at once:
 //   - the tile's rows are loaded into registers one tile ahead (32 bytes per
 //     thread, one thread per 32-pixel word) and packed into a
 //     1-bit-per-pixel plane;
@@ -29,7 +30,7 @@
 namespace ccl {
 
 // rootinfo layout: bits 0-15 local pixel index of the root's first pixel
-// (row * 1024 + column), bit 16 foreground, bit 17 touches a tile edge,
+// (row * tile width + column), bit 16 foreground, bit 17 touches a tile edge,
 // bits 18-29 border ordinal of the root within the tile, bit 30 the
 // component has a single run in the tile.
 constexpr int RI_FG = 16, RI_BORDER = 17, RI_KB = 18, RI_SINGLE = 30;
@@ -44,7 +45,7 @@ __global__ void k_prologue(Batch B) {
         // per tile: its image, and where its rows start for the row loads
         const int img = image_of_tile(B, i);
         const ImgDesc &d = B.desc[img];
-        const TileGeo g = tile_geo(d, i - d.tile0, B.th);
+        const TileGeo g = tile_geo(d, i - d.tile0, B.th, B.tw);
         const uint64_t src = (uint64_t)(d.img + (int64_t)g.y0 * d.pitch + g.x0);
         B.s.tstat[i] = make_int4(0, 0, 0, img);
         B.s.tsrc[i] = make_int4((int)(uint32_t)src, (int)(uint32_t)(src >> 32), d.pitch,
@@ -52,7 +53,7 @@ __global__ void k_prologue(Batch B) {
         TileHdr h;
         h.px = g.px;
         h.b = g.b;
-        h.b_above = g.ty > 0 ? tile_geo(d, i - d.tile0 - d.TX, B.th).b : 0;
+        h.b_above = g.ty > 0 ? tile_geo(d, i - d.tile0 - d.TX, B.th, B.tw).b : 0;
         h.seg0 = d.seg0;
         h.img = img;
         h.tx = g.tx;
@@ -144,18 +145,22 @@ __device__ __forceinline__ void run_union(uint32_t *par, uint32_t a, uint32_t b,
     *ok = false;
 }
 
-// Tile geometry of the labeller: TH rows x 1024 columns, one thread per
-// 32-pixel word (NT threads), up to NPX runs.
-template <int TH> struct LabelCfg {
+// Tile geometry of the labeller: TH rows x TW columns (WPR = TW / 32 words
+// per row; a warp holds 32 / WPR rows), one thread per 32-pixel word (NT
+// threads), up to NPX runs.
+template <int TH, int TW> struct LabelCfg {
+    static constexpr int WPR = TW / 32;
+    static constexpr int LOG_TW = TW == 1024 ? 10 : 9;
     static constexpr int NT = TH * WPR;       // threads = words of a tile
     static constexpr int NW = NT / 32;        // warps
     static constexpr int NPX = TH * TW;       // pixels = most runs
     static constexpr int KMAX = NPX / NT;     // rounds of the per-run loops (32)
+    static_assert(TW == 512 || TW == 1024, "tile widths");
 };
 
-template <int TH>
+template <int TH, int TW>
 constexpr size_t label_smem() {
-    using C = LabelCfg<TH>;
+    using C = LabelCfg<TH, TW>;
     return (size_t)C::NPX * 4            // par
            + (size_t)C::NPX * 2          // run list
            + (size_t)C::NPX / 8          // border flags per run
@@ -166,16 +171,19 @@ constexpr size_t label_smem() {
 
 // End column (exclusive) of run i of row r: the next run's start on the same
 // row, else the tile width.
+template <int TW>
 __device__ __forceinline__ int run_end(const uint16_t *list, int i, int n, int r, int tw) {
+    constexpr int LOG_TW = TW == 1024 ? 10 : 9;
     if (i + 1 < n) {
         const int pn = (int)(list[i + 1] >> 1);
-        if ((pn >> 10) == r) return pn & (TW - 1);
+        if ((pn >> LOG_TW) == r) return pn & (TW - 1);
     }
     return tw;
 }
 
 // Ordinal of the run covering column x of row r (the word holds a run start
 // at or before x, or the run started in an earlier word of the row).
+template <int WPR>
 __device__ __forceinline__ int ord_at(const uint16_t *sOrd, const uint32_t *sE, int r, int x) {
     const int wi = r * WPR + (x >> 5);
     return (int)sOrd[wi] + __popc(sE[wi] & mask_le(x & 31)) - 1;
@@ -184,13 +192,13 @@ __device__ __forceinline__ int ord_at(const uint16_t *sOrd, const uint32_t *sE, 
 // Same-colour runs of row rr that touch run [s, e) of colour c (rr = the row
 // above or below): the ordinal range [*jf, *jl], every other ordinal. An
 // 8-adjacent colour's window is widened by one pixel on each side.
-template <int CONN>
+template <int CONN, int WPR>
 __device__ __forceinline__ void touching(const uint16_t *sOrd, const uint32_t *sE, const uint32_t *sC, int rr,
                                          int s, int e, uint32_t c, int tw, int *jf, int *jl) {
     const int adj8 = CONN ? (int)(c ^ 1u) : (int)c;
     const int xa = max(s - adj8, 0), xb = min(e - 1 + adj8, tw - 1);
-    const int oa = ord_at(sOrd, sE, rr, xa);
-    const int ob = ord_at(sOrd, sE, rr, xb);
+    const int oa = ord_at<WPR>(sOrd, sE, rr, xa);
+    const int ob = ord_at<WPR>(sOrd, sE, rr, xb);
     const uint32_t ca = (sC[rr * WPR + (xa >> 5)] >> (xa & 31)) & 1u;
     *jf = oa + (int)(ca != c);
     *jl = ob;
@@ -205,10 +213,10 @@ __device__ __forceinline__ void touching(const uint16_t *sOrd, const uint32_t *s
 // (in raster order of their first pixel), then the single-run roots; the
 // feature pass keeps on-chip records for the former only. Border ordinals
 // (roots touching a tile edge) are handed out in any order.
-template <int CONN, int TH>
-__global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Batch B) {
-    using C = LabelCfg<TH>;
-    constexpr int NT = C::NT, NW = C::NW, NPX = C::NPX, KMAX = C::KMAX;
+template <int CONN, int TH, int TW>
+__global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>::NT) k_label(Batch B) {
+    using C = LabelCfg<TH, TW>;
+    constexpr int NT = C::NT, NW = C::NW, NPX = C::NPX, KMAX = C::KMAX, WPR = C::WPR, LOG_TW = C::LOG_TW;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *par = (uint32_t *)smem;                         // [NPX]
     uint16_t *list = (uint16_t *)(par + NPX);                 // [NPX] pixel index << 1 | colour
@@ -283,7 +291,7 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
             word = (nz16(v0) | (nz16(v1) << 16)) & vm;
             if (r_w < th) B.s.fgbits[plane0 + r_w * rowwords + l_w] = word;
             sC[tid] = word;
-            // runs never cross a tile's left edge (one warp = one row)
+            // runs never cross a tile's left edge (a warp holds whole rows)
             const uint32_t left = __shfl_up_sync(FULL, word, 1);
             const uint32_t prev = (word << 1) | (l_w ? (left >> 31) : 0u);
             e = ((word ^ prev) | (l_w == 0 ? 1u : 0u)) & vm;
@@ -323,11 +331,11 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
         // the classes.
         for (int i = tid; i < n; i += NT) {
             const uint32_t v = list[i];
-            const int pix = (int)(v >> 1), r = pix >> 10, s = pix & (TW - 1);
+            const int pix = (int)(v >> 1), r = pix >> LOG_TW, s = pix & (TW - 1);
             if (r == 0) continue;
-            const int e_ = run_end(list, i, n, r, tw);
+            const int e_ = run_end<TW>(list, i, n, r, tw);
             int jf, jl;
-            touching<CONN>(sOrd, sE, sC, r - 1, s, e_, v & 1u, tw, &jf, &jl);
+            touching<CONN, WPR>(sOrd, sE, sC, r - 1, s, e_, v & 1u, tw, &jf, &jl);
             for (int j = jf; j <= jl; j += 2) run_union(par, (uint32_t)i, (uint32_t)j, &ok);
         }
         // the rows of the next tile: their loads complete during the rest of
@@ -346,8 +354,8 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
             bool is_root = false, multi = false;
             if (i < n) {
                 const uint32_t v = list[i];
-                const int pix = (int)(v >> 1), r = pix >> 10, s = pix & (TW - 1);
-                const int e_ = run_end(list, i, n, r, tw);
+                const int pix = (int)(v >> 1), r = pix >> LOG_TW, s = pix & (TW - 1);
+                const int e_ = run_end<TW>(list, i, n, r, tw);
                 const uint32_t p = ld_par(par, (uint32_t)i);
                 const uint32_t root = p == (uint32_t)i ? p : run_find(par, p, &ok);
                 if (root != p) par[i] = root;
@@ -355,7 +363,7 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
                 if (r == 0 || r == th - 1 || s == 0 || e_ == tw) atomicOr(&sBrd[root >> 5], 1u << (root & 31));
                 if (is_root && r + 1 < th) {
                     int jf, jl;
-                    touching<CONN>(sOrd, sE, sC, r + 1, s, e_, v & 1u, tw, &jf, &jl);
+                    touching<CONN, WPR>(sOrd, sE, sC, r + 1, s, e_, v & 1u, tw, &jf, &jl);
                     multi = jf <= jl;
                 }
             }
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
                 if (border) {
                     const int kb = kb0 + __popc(bb & lt);
                     const uint32_t slot = slot0 + kb;
-                    const int r = pix >> 10, s = pix & (TW - 1);
+                    const int r = pix >> LOG_TW, s = pix & (TW - 1);
                     const int64_t key = (int64_t)(y0 + r) * h.w + x0 + s;
                     B.s.gp[slot] = ((unsigned long long)(key + 1) << 32) | slot;
                     B.s.binfo[slot] = (uint32_t)kk | (fg << 16);
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(LabelCfg<TH>::NT, TH == 32 ? 1 : 2) k_label(Ba
             else if (i < 2 * tw) { r = th - 1; c = i - tw; }
             else if (i < 2 * tw + th) { r = i - 2 * tw; c = 0; }
             else { r = i - 2 * tw - th; c = tw - 1; }
-            uint32_t v = ld_par(par, (uint32_t)ord_at(sOrd, sE, r, c));
+            uint32_t v = ld_par(par, (uint32_t)ord_at<WPR>(sOrd, sE, r, c));
             if (!(v & PAR_TAG)) v = ld_par(par, v);
             eg[i] = (uint16_t)((v >> 15) & 0xFFFu);
         }
@@ -482,20 +490,27 @@ void launch_prologue(const Batch &B, cudaStream_t st) {
     k_prologue<<<(n + 255) / 256, 256, 0, st>>>(B);
 }
 
-void launch_label(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    if (B.th == 32) {
-        const int grid = min(B.n_tiles, c.sms);
-        if (B.conn == 0)
-            k_label<0, 32><<<grid, LabelCfg<32>::NT, label_smem<32>(), st>>>(B);
-        else
-            k_label<1, 32><<<grid, LabelCfg<32>::NT, label_smem<32>(), st>>>(B);
+template <int CONN, int TH, int TW>
+static void launch_label_shape(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
+    using C = LabelCfg<TH, TW>;
+    const int grid = min(B.n_tiles, (1024 / C::NT) * c.sms);
+    k_label<CONN, TH, TW><<<grid, C::NT, label_smem<TH, TW>(), st>>>(B);
+}
+
+template <int CONN>
+static void launch_label_conn(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
+    if (B.tw == 1024) {
+        if (B.th == 32) launch_label_shape<CONN, 32, 1024>(B, c, st);
+        else launch_label_shape<CONN, 16, 1024>(B, c, st);
     } else {
-        const int grid = min(B.n_tiles, 2 * c.sms);
-        if (B.conn == 0)
-            k_label<0, 16><<<grid, LabelCfg<16>::NT, label_smem<16>(), st>>>(B);
-        else
-            k_label<1, 16><<<grid, LabelCfg<16>::NT, label_smem<16>(), st>>>(B);
+        if (B.th == 32) launch_label_shape<CONN, 32, 512>(B, c, st);
+        else launch_label_shape<CONN, 16, 512>(B, c, st);
     }
+}
+
+void launch_label(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
+    if (B.conn == 0) launch_label_conn<0>(B, c, st);
+    else launch_label_conn<1>(B, c, st);
 }
 
 template <typename K>
@@ -505,11 +520,18 @@ static cudaError_t configure_smem(K kernel, size_t bytes) {
     return e;
 }
 
+template <int CONN>
+static cudaError_t configure_label_conn() {
+    cudaError_t e = configure_smem(k_label<CONN, 32, 1024>, label_smem<32, 1024>());
+    if (e == cudaSuccess) e = configure_smem(k_label<CONN, 16, 1024>, label_smem<16, 1024>());
+    if (e == cudaSuccess) e = configure_smem(k_label<CONN, 32, 512>, label_smem<32, 512>());
+    if (e == cudaSuccess) e = configure_smem(k_label<CONN, 16, 512>, label_smem<16, 512>());
+    return e;
+}
+
 cudaError_t configure_label() {
-    cudaError_t e = configure_smem(k_label<0, 32>, label_smem<32>());
-    if (e == cudaSuccess) e = configure_smem(k_label<1, 32>, label_smem<32>());
-    if (e == cudaSuccess) e = configure_smem(k_label<0, 16>, label_smem<16>());
-    if (e == cudaSuccess) e = configure_smem(k_label<1, 16>, label_smem<16>());
+    cudaError_t e = configure_label_conn<0>();
+    if (e == cudaSuccess) e = configure_label_conn<1>();
     return e;
 }
 

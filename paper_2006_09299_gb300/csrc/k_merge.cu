@@ -42,7 +42,7 @@ __device__ __forceinline__ uint32_t edge_slot(const Batch &B, const ImgDesc &d, 
 }
 
 __device__ __forceinline__ uint32_t plane_word(const Batch &B, const ImgDesc &d, int y, int j) {
-    return B.s.fgbits[(d.seg0 + (int64_t)y * d.TX) * WPR + j];
+    return B.s.fgbits[(d.seg0 + (int64_t)y * d.TX) * B.wpr + j];
 }
 
 __device__ __forceinline__ bool pixel_fg(const Batch &B, const ImgDesc &d, int y, int x) {
@@ -50,15 +50,16 @@ __device__ __forceinline__ bool pixel_fg(const Batch &B, const ImgDesc &d, int y
 }
 
 // Run starts of a row word, with a forced start at every tile column start
-// (runs never cross a tile's left edge).
-__device__ __forceinline__ uint32_t starts(uint32_t c, uint32_t cl, int j, uint32_t vm) {
+// (runs never cross a tile's left edge; wpr words per tile row).
+__device__ __forceinline__ uint32_t starts(uint32_t c, uint32_t cl, int j, int wpr, uint32_t vm) {
     const uint32_t prev = (c << 1) | (cl >> 31);
-    return ((c ^ prev) | ((j & 31) == 0 ? 1u : 0u)) & vm;
+    return ((c ^ prev) | ((j & (wpr - 1)) == 0 ? 1u : 0u)) & vm;
 }
 
 template <int CONN>
 __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool *ok) {
-    const int64_t words = (int64_t)d.TX * WPR;
+    const int64_t words = (int64_t)d.TX * B.wpr;
+    const int lt = B.log_tw, tm = B.tw - 1;
     const int hs = B.hsplit;
     const int part = (int)(item % hs);   // columns [part, part + 1) x 32 / hsplit of the word
     item /= hs;
@@ -75,7 +76,7 @@ __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool 
     const uint32_t cul = j ? plane_word(B, d, yu, j - 1) : 0u, cdl = j ? plane_word(B, d, yd, j - 1) : 0u;
     const uint32_t cur = (j + 1) < words ? plane_word(B, d, yu, j + 1) : 0u;
     const uint32_t cdr = (j + 1) < words ? plane_word(B, d, yd, j + 1) : 0u;
-    const uint32_t eu = starts(cu, cul, j, vm), ed = starts(cd, cdl, j, vm);
+    const uint32_t eu = starts(cu, cul, j, B.wpr, vm), ed = starts(cd, cdl, j, B.wpr, vm);
     const uint32_t vml = FULL;   // the word to the left is always fully valid
     const uint32_t vmr = (x + 32 < d.w) ? (d.w - x - 32 >= 32 ? FULL : ((1u << (d.w - x - 32)) - 1u)) : 0u;
     const uint32_t ad = CONN ? (~cd & vm) : cd, au = CONN ? (~cu & vm) : cu;
@@ -93,24 +94,24 @@ __device__ void merge_rows(const Batch &B, const ImgDesc &d, int64_t item, bool 
     while (m) {
         const int xx = x + __ffs(m) - 1;
         m &= m - 1;
-        global_union(B.s.gp, edge_slot(B, d, ltd + (xx >> 10), TOP, xx & 1023),
-                     edge_slot(B, d, ltu + (xx >> 10), BOTTOM, xx & 1023), ok);
+        global_union(B.s.gp, edge_slot(B, d, ltd + (xx >> lt), TOP, xx & tm),
+                     edge_slot(B, d, ltu + (xx >> lt), BOTTOM, xx & tm), ok);
     }
     m = d1;
     while (m) {
         const int xx = x + __ffs(m) - 1;
         m &= m - 1;
         const int xu = xx + 1;
-        global_union(B.s.gp, edge_slot(B, d, ltd + (xx >> 10), TOP, xx & 1023),
-                     edge_slot(B, d, ltu + (xu >> 10), BOTTOM, xu & 1023), ok);
+        global_union(B.s.gp, edge_slot(B, d, ltd + (xx >> lt), TOP, xx & tm),
+                     edge_slot(B, d, ltu + (xu >> lt), BOTTOM, xu & tm), ok);
     }
     m = d2;
     while (m) {
         const int xx = x + __ffs(m) - 1;
         m &= m - 1;
         const int xu = xx - 1;
-        global_union(B.s.gp, edge_slot(B, d, ltd + (xx >> 10), TOP, xx & 1023),
-                     edge_slot(B, d, ltu + (xu >> 10), BOTTOM, xu & 1023), ok);
+        global_union(B.s.gp, edge_slot(B, d, ltd + (xx >> lt), TOP, xx & tm),
+                     edge_slot(B, d, ltu + (xu >> lt), BOTTOM, xu & tm), ok);
     }
 }
 
@@ -118,7 +119,7 @@ template <int CONN>
 __device__ void merge_cols(const Batch &B, const ImgDesc &d, int64_t item, bool *ok) {
     const int vb = (int)(item / d.h);          // boundary between tile columns vb and vb+1
     const int y = (int)(item - (int64_t)vb * d.h);
-    const int x0 = (vb + 1) * TW;
+    const int x0 = (vb + 1) * B.tw;
     const int ty = y / B.th, r = y - ty * B.th;
     const int th = min(B.th, d.h - ty * B.th);
     const int ltl = ty * d.TX + vb, ltr = ltl + 1;
@@ -142,7 +143,7 @@ __device__ void merge_cols(const Batch &B, const ImgDesc &d, int64_t item, bool 
 
 // Background cells on the image border belong to the exterior.
 __device__ void merge_perimeter(const Batch &B, const ImgDesc &d, int img, int64_t item, bool *ok) {
-    const int64_t words = (int64_t)d.TX * WPR;
+    const int64_t words = (int64_t)d.TX * B.wpr;
     const uint32_t ext = (uint32_t)img;
     if (item < 2 * words) {
         const bool bottom = item >= words;
@@ -156,13 +157,14 @@ __device__ void merge_perimeter(const Batch &B, const ImgDesc &d, int img, int64
         const uint32_t cl = j ? plane_word(B, d, y, j - 1) : FULL;
         const uint32_t bg = ~c & vm, bgl = ~cl;
         const uint32_t bprev = (bg << 1) | (bgl >> 31);
-        const uint32_t st = (bg & ~bprev) | ((j & 31) == 0 ? (bg & 1u) : 0u);
+        const uint32_t st = (bg & ~bprev) | ((j & (B.wpr - 1)) == 0 ? (bg & 1u) : 0u);
         const int lt0 = bottom ? (d.TY - 1) * d.TX : 0;
         uint32_t m = st;
         while (m) {
             const int xx = x + __ffs(m) - 1;
             m &= m - 1;
-            global_union(B.s.gp, edge_slot(B, d, lt0 + (xx >> 10), bottom ? BOTTOM : TOP, xx & 1023), ext, ok);
+            global_union(B.s.gp, edge_slot(B, d, lt0 + (xx >> B.log_tw), bottom ? BOTTOM : TOP, xx & (B.tw - 1)),
+                         ext, ok);
         }
         return;
     }
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
             } else {
                 const int64_t key = (int64_t)(B.s.gp[slot] >> 32) - 1;
                 const int y = (int)(key / h.w), x = (int)(key - (int64_t)y * h.w);
-                atomicOr(&B.s.nodebits[(h.seg0 + (int64_t)y * h.TX) * WPR + (x >> 5)], 1u << (x & 31));
+                atomicOr(&B.s.nodebits[(h.seg0 + (int64_t)y * h.TX) * B.wpr + (x >> 5)], 1u << (x & 31));
                 nfg += (B.s.binfo[slot] >> 16) & 1;
             }
         }
@@ -230,20 +232,21 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
     }
 }
 
-// Node count of every segment (one tile row: 32 words of the node plane).
+// Node count of every segment (one tile row: wpr words of the node plane).
 __global__ void __launch_bounds__(SCAN_B) k_scan_count(Batch B) {
     __shared__ int sPart[SCAN_B / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
     int c = 0;
     if (s < B.n_segs) {
-        // one segment per thread: its 32 words in eight independent vector loads
-        const uint4 *w4 = reinterpret_cast<const uint4 *>(B.s.nodebits + s * WPR);
-        uint4 v[8];
+        // one segment per thread: its words in independent vector loads
+        const uint4 *w4 = reinterpret_cast<const uint4 *>(B.s.nodebits + s * B.wpr);
+        const int nq = B.wpr / 4;
+        uint4 v[WPR_MAX / 4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = w4[q];
+        for (int q = 0; q < WPR_MAX / 4; ++q) v[q] = q < nq ? w4[q] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) c += __popc(v[q].x) + __popc(v[q].y) + __popc(v[q].z) + __popc(v[q].w);
+        for (int q = 0; q < WPR_MAX / 4; ++q) c += __popc(v[q].x) + __popc(v[q].y) + __popc(v[q].z) + __popc(v[q].w);
         B.s.seg_cnt[s] = c;
     }
     const int wsum = warp_sum(c);
@@ -304,10 +307,10 @@ __global__ void __launch_bounds__(SCAN_B) k_scan_apply(Batch B) {
 // Node id of the component whose first pixel has raster index key.
 __device__ __forceinline__ int node_id_of_key(const Batch &B, const ImgDesc &d, int64_t key) {
     const int y = (int)(key / d.w), x = (int)(key - (int64_t)y * d.w);
-    const int64_t s = d.seg0 + (int64_t)y * d.TX + (x >> 10);
+    const int64_t s = d.seg0 + (int64_t)y * d.TX + (x >> B.log_tw);
     int id = 1 + B.s.seg_base[s] - B.s.seg_base[d.seg0];
-    const uint32_t *w = B.s.nodebits + s * WPR;
-    const int l = (x & 1023) >> 5;
+    const uint32_t *w = B.s.nodebits + s * B.wpr;
+    const int l = (x & (B.tw - 1)) >> 5;
     for (int k = 0; k < l; ++k) id += __popc(w[k]);
     return id + __popc(w[l] & mask_lt(x & 31));
 }

@@ -24,26 +24,34 @@
 
 namespace ccl {
 
-// Launch shape per tile height: NT threads, each holding two 32-pixel words
-// of the tile (a warp holds rows w and w + NT / 32), several CTAs per SM so
-// that one streams its label rows while another computes. Root ordinals of a
+// Launch shape per tile shape (TH rows x TW columns, WPR = TW / 32 words per
+// row): NT threads, each holding two 32-pixel words of the tile (word t and
+// word t + NT, so a warp holds 32 / WPR rows in each half of the tile),
+// several CTAs per SM so that one streams its label rows while another
+// computes. Root ordinals of a
 // tile put the roots of components with several runs first, then the
 // single-run roots. Multi-run roots below MAXR accumulate their features in
 // on-chip records (more spill to global atomics); node ids of the first
 // MAXID roots are kept on chip (the rest are computed when needed);
 // 2^HASH_BITS entries combine the feature contributions of border roots.
-template <int TH> struct WriteCfg;
-template <> struct WriteCfg<32> {
+template <int TH, int TW> struct WriteCfg;
+template <> struct WriteCfg<32, 1024> {
     static constexpr int NT = 512, MAXR = 2048, MAXID = 8192, HASH_BITS = 9, CTAS = 2;
 };
-template <> struct WriteCfg<16> {
+template <> struct WriteCfg<16, 1024> {
     static constexpr int NT = 256, MAXR = 1024, MAXID = 3072, HASH_BITS = 8, CTAS = 4;
 };
+template <> struct WriteCfg<32, 512> {
+    static constexpr int NT = 256, MAXR = 1024, MAXID = 3072, HASH_BITS = 8, CTAS = 4;
+};
+template <> struct WriteCfg<16, 512> {
+    static constexpr int NT = 128, MAXR = 512, MAXID = 1536, HASH_BITS = 7, CTAS = 8;
+};
 
-template <int TH>
+template <int TH, int TW>
 constexpr size_t write_smem() {
-    using C = WriteCfg<TH>;
-    constexpr size_t NWD = (size_t)TH * WPR;
+    using C = WriteCfg<TH, TW>;
+    constexpr size_t NWD = (size_t)TH * (TW / 32);
     return (size_t)C::MAXR * 6 * 4                // records
            + (size_t)C::MAXID * 4                 // node id per root
            + 3 * NWD * 4                          // colour, run-start and node-bit planes
@@ -131,6 +139,21 @@ __device__ __forceinline__ void cp_async_wait_all_w() { asm volatile("cp.async.w
 __device__ __forceinline__ int rec_root(uint32_t v) { return (int)(v >> 16); }
 __device__ __forceinline__ int rec_pix(uint32_t v) { return (int)((v >> 1) & 0x7FFFu); }
 
+// Exclusive prefix sum over segments of W consecutive lanes (one tile row);
+// *total receives the segment's sum.
+template <int W>
+__device__ __forceinline__ int seg_excl_sum(int v, int *total) {
+    const int l = threadIdx.x & (W - 1);
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < W; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o, W);
+        if (l >= o) x += y;
+    }
+    *total = __shfl_sync(FULL, x, W - 1, W);
+    return x - v;
+}
+
 // The bit-plane words of one tile held by one thread (two words), loaded
 // one tile ahead.
 struct PlaneRegs {
@@ -142,10 +165,11 @@ struct PlaneRegs {
 // the headers and counts of the tile after next into shared memory; the bit
 // planes of the next tile are loaded into registers while the CTA works on
 // the current one.
-template <int TH>
-__global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(Batch B) {
-    using C = WriteCfg<TH>;
-    constexpr int NT = C::NT, NW = NT / 32, NWD = TH * WPR, MAXR = C::MAXR, MAXID = C::MAXID;
+template <int TH, int TW>
+__global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) k_write(Batch B) {
+    using C = WriteCfg<TH, TW>;
+    constexpr int WPR = TW / 32, LOG_TW = TW == 1024 ? 10 : 9;
+    constexpr int NT = C::NT, NWD = TH * WPR, MAXR = C::MAXR, MAXID = C::MAXID;
     constexpr int HN = 1 << C::HASH_BITS;
     static_assert(NWD == 2 * NT, "two words per thread");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -168,23 +192,24 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
     __shared__ int4 sSt[3];
     const TileHash<C::HASH_BITS> H(hmem);
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int l = tid % WPR;   // this thread's word within its rows (word tid and word tid + NT)
 
     auto load_planes = [&](const TileHdr &h, PlaneRegs &p) {
         const int64_t rowwords = (int64_t)h.TX * WPR;
         const int64_t plane0 = (h.seg0 + (int64_t)h.y0 * h.TX + h.tx) * WPR;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int r = warp + j * NW;
+            const int r = (tid + j * NT) / WPR;
             p.c[j] = p.nb[j] = 0u;
             p.seg[j] = 0;
             if (r < h.th) {
-                p.c[j] = B.s.fgbits[plane0 + r * rowwords + lane];
-                p.nb[j] = B.s.nodebits[plane0 + r * rowwords + lane];
-                if (lane == 0) p.seg[j] = B.s.seg_base[h.seg0 + (int64_t)(h.y0 + r) * h.TX + h.tx];
+                p.c[j] = B.s.fgbits[plane0 + r * rowwords + l];
+                p.nb[j] = B.s.nodebits[plane0 + r * rowwords + l];
+                if (l == 0) p.seg[j] = B.s.seg_base[h.seg0 + (int64_t)(h.y0 + r) * h.TX + h.tx];
             }
         }
-        p.seg_first = lane == 0 ? B.s.seg_base[h.seg0] : 0;
+        p.seg_first = l == 0 ? B.s.seg_base[h.seg0] : 0;
     };
 
     int nc = 0;   // thread 0: the tile claimed for two iterations on
@@ -244,20 +269,20 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
         int rex[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int r = warp + j * NW, word = tid + j * NT;
+            const int word = tid + j * NT, r = word / WPR;
             const uint32_t c = pr.c[j];
-            const int vcnt = min(max(tw - 32 * lane, 0), 32);
+            const int vcnt = min(max(tw - 32 * l, 0), 32);
             const uint32_t vr = r < th ? (vcnt >= 32 ? FULL : ((1u << vcnt) - 1u)) : 0u;
             const uint32_t left = __shfl_up_sync(FULL, c, 1);
-            const uint32_t prev = (c << 1) | (lane ? (left >> 31) : 0u);
-            const uint32_t e = ((c ^ prev) | (lane == 0 ? 1u : 0u)) & vr;
+            const uint32_t prev = (c << 1) | (l ? (left >> 31) : 0u);
+            const uint32_t e = ((c ^ prev) | (l == 0 ? 1u : 0u)) & vr;
             sC[word] = c;
             sE[word] = e;
             sNB[word] = pr.nb[j];
             int ntot, rtot;
-            sNBPre[word] = (uint16_t)warp_excl_sum(__popc(pr.nb[j]), &ntot);
-            rex[j] = warp_excl_sum(__popc(e), &rtot);
-            if (lane == 0) {
+            sNBPre[word] = (uint16_t)seg_excl_sum<WPR>(__popc(pr.nb[j]), &ntot);
+            rex[j] = seg_excl_sum<WPR>(__popc(e), &rtot);
+            if (l == 0) {
                 sRowTot[r] = rtot;
                 sRowSeg[r] = r < th ? pr.seg[j] - pr.seg_first : 0;
             }
@@ -272,7 +297,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
             n = wt;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int r = warp + j * NW;
+                const int r = (tid + j * NT) / WPR;
                 sOrd[tid + j * NT] = (uint16_t)(__shfl_sync(FULL, ex, r) + rex[j]);
             }
             if (tid == 0) sOrd[NWD] = (uint16_t)n;
@@ -291,7 +316,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
         auto root_id = [&](uint32_t info) -> int {
             const int idx = info & 0xFFFF;
             if (!((info >> 17) & 1u)) {
-                const int r = idx >> 10, c = idx & 1023, wi = r * WPR + (c >> 5);
+                const int r = idx >> LOG_TW, c = idx & (TW - 1), wi = r * WPR + (c >> 5);
                 return 1 + sRowSeg[r] + (int)sNBPre[wi] + __popc(sNB[wi] & mask_lt(c & 31));
             }
             const uint32_t root = (uint32_t)B.s.gp[slot0 + ((info >> 18) & 0xFFFu)];
@@ -314,7 +339,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
             if (k < n_multi && k >= MAXR && !((info >> 17) & 1u) && id < cap) {
                 d.feat[0 * cap + id] = 0;
                 d.feat[1 * cap + id] = INT64_MAX;
-                d.feat[2 * cap + id] = y0 + ((info & 0xFFFF) >> 10);
+                d.feat[2 * cap + id] = y0 + ((info & 0xFFFF) >> LOG_TW);
                 d.feat[3 * cap + id] = -1;
                 d.feat[4 * cap + id] = -1;
                 d.feat[5 * cap + id] = 0;
@@ -327,25 +352,25 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
         if (B.labels && d.fg != nullptr) {
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
-                const int r = warp + j * NW;
+                const int r = (tid + j * NT) / WPR;
                 if (r >= th) break;
                 int32_t *fgrow = d.fg + (int64_t)(y0 + r) * h.w + x0;
                 int32_t *bgrow = d.bg + (int64_t)(y0 + r) * h.w + x0;
-                constexpr int G = TW / 128, GB = 4;   // groups per lane, groups per batch
+                constexpr int G = TW / (4 * WPR), GB = 4;   // groups per lane, groups per batch
 #pragma unroll 1
                 for (int g0 = 0; g0 < G; g0 += GB) {
                     int q0[GB];
                     uint32_t v0[GB];
 #pragma unroll
                     for (int u = 0; u < GB; ++u) {
-                        const int x = 128 * (g0 + u) + 4 * lane;
+                        const int x = 4 * WPR * (g0 + u) + 4 * l;
                         q0[u] = x < tw ? ord_at(r, x) : -1;
                         v0[u] = q0[u] >= 0 ? rr[q0[u]] : 0u;
                     }
 #pragma unroll
                     for (int u = 0; u < GB; ++u) {
                         if (q0[u] < 0) continue;
-                        const int x = 128 * (g0 + u) + 4 * lane;
+                        const int x = 4 * WPR * (g0 + u) + 4 * l;
                         const int wi = r * WPR + (x >> 5), b = x & 31;
                         const uint32_t ew = sE[wi], cw = sC[wi];
                         // run starts inside the group (usually none: one lookup)
@@ -403,12 +428,12 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
             // the next run's start: the next lane's record
             uint32_t vn = __shfl_down_sync(FULL, v, 1);
             if (lane == 31) vn = vl;
-            const int k = rec_root(v), pix = rec_pix(v), r = pix >> 10, s = pix & (TW - 1);
+            const int k = rec_root(v), pix = rec_pix(v), r = pix >> LOG_TW, s = pix & (TW - 1);
             const bool multi = i < n && k < n_multi;
             int en = tw;
             if (i + 1 < n) {
                 const int pn = rec_pix(vn);
-                if ((pn >> 10) == r) en = pn & (TW - 1);
+                if ((pn >> LOG_TW) == r) en = pn & (TW - 1);
             }
             uint32_t len = 0, sx = 0;
             uint32_t key = 0xFFFFFFFFu;   // (root, row) of a multi-run root on chip
@@ -460,7 +485,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
         // tile above (or the exterior on the image's top row)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int r = warp + j * NW, word = tid + j * NT;
+            const int word = tid + j * NT, r = word / WPR;
             const uint32_t nbw = sNB[word];
             uint32_t m = nbw;
             while (m) {
@@ -471,14 +496,14 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
                 for (int u = 0; u < 2; ++u) {
                     bb[u] = m ? __ffs(m) - 1 : -1;
                     if (m) m &= m - 1;
-                    pq[u] = bb[u] >= 0 && r > 0 ? ord_at(r - 1, 32 * lane + bb[u]) : -1;
+                    pq[u] = bb[u] >= 0 && r > 0 ? ord_at(r - 1, 32 * l + bb[u]) : -1;
                     if (pq[u] >= 0) pv[u] = rr[pq[u]];
                 }
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int b = bb[u];
                     if (b < 0) continue;
-                    const int c = 32 * lane + b;
+                    const int c = 32 * l + b;
                     const int id = 1 + sRowSeg[r] + (int)sNBPre[word] + __popc(nbw & mask_lt(b));
                     int p = 0;
                     if (r > 0) {
@@ -507,7 +532,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
             const uint32_t info = fin_nx;
             if (k + NT < n_roots) fin_nx = ri[k + NT];
             if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
-            const int idx = info & 0xFFFF, r = idx >> 10, c = idx & 1023;
+            const int idx = info & 0xFFFF, r = idx >> LOG_TW, c = idx & (TW - 1);
             const bool isb = (info >> 17) & 1u;
             const int id = id_of(k);
             if (id >= cap) continue;
@@ -526,7 +551,7 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
                 int ce = tw;
                 if (qr + 1 < n) {
                     const int pn = rec_pix(rr[qr + 1]);
-                    if ((pn >> 10) == r) ce = pn & (TW - 1);
+                    if ((pn >> LOG_TW) == r) ce = pn & (TW - 1);
                 }
                 la = (uint32_t)(ce - c);
                 lsx = (uint32_t)((c + ce - 1) * (ce - c) / 2);
@@ -579,19 +604,35 @@ __global__ void __launch_bounds__(WriteCfg<TH>::NT, WriteCfg<TH>::CTAS) k_write(
     }
 }
 
+template <int TH, int TW>
+static void launch_write_shape(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
+    using C = WriteCfg<TH, TW>;
+    k_write<TH, TW><<<min(B.n_tiles, C::CTAS * c.sms), C::NT, write_smem<TH, TW>(), st>>>(B);
+}
+
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    if (B.th == 32)
-        k_write<32><<<min(B.n_tiles, WriteCfg<32>::CTAS * c.sms), WriteCfg<32>::NT, write_smem<32>(), st>>>(B);
-    else
-        k_write<16><<<min(B.n_tiles, WriteCfg<16>::CTAS * c.sms), WriteCfg<16>::NT, write_smem<16>(), st>>>(B);
+    if (B.tw == 1024) {
+        if (B.th == 32) launch_write_shape<32, 1024>(B, c, st);
+        else launch_write_shape<16, 1024>(B, c, st);
+    } else {
+        if (B.th == 32) launch_write_shape<32, 512>(B, c, st);
+        else launch_write_shape<16, 512>(B, c, st);
+    }
+}
+
+template <int TH, int TW>
+static cudaError_t configure_write_shape() {
+    cudaError_t e = cudaFuncSetAttribute(k_write<TH, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)write_smem<TH, TW>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_write<TH, TW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
 }
 
 cudaError_t configure_write() {
-    cudaError_t e = cudaFuncSetAttribute(k_write<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)write_smem<32>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_write<32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_write<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)write_smem<16>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_write<16>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = configure_write_shape<32, 1024>();
+    if (e == cudaSuccess) e = configure_write_shape<16, 1024>();
+    if (e == cudaSuccess) e = configure_write_shape<32, 512>();
+    if (e == cudaSuccess) e = configure_write_shape<16, 512>();
     return e;
 }
 

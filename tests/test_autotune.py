@@ -7,11 +7,13 @@ from paper_2006_09299_gb300 import autotune, inputs
 
 class FakeCtx:
     def __init__(self):
-        self.rows = None
-        self.split = None
+        self.rows = self.cols = self.split = None
 
     def set_tile_rows(self, rows):
         self.rows = rows
+
+    def set_tile_cols(self, cols):
+        self.cols = cols
 
     def set_merge_split(self, split):
         self.split = split
@@ -19,22 +21,24 @@ class FakeCtx:
 
 def test_tune_picks_fastest_shape_and_schedule_and_caches(tmp_path):
     ctx = FakeCtx()
-    cost = {(32, 4): 2.0, (16, 4): 1.5, (16, 1): 1.6, (16, 2): 1.4, (16, 8): 1.45, (32, 1): 0.1, (32, 2): 0.9,
-            (32, 8): 0.8}
-    timer = lambda fn, reps: cost[(ctx.rows, ctx.split)]
+    cost = {(32, 1024, 4): 2.0, (16, 1024, 4): 1.5, (32, 512, 4): 1.7, (16, 512, 4): 1.6,
+            (16, 1024, 1): 1.6, (16, 1024, 2): 1.4, (16, 1024, 8): 1.45}
+    timer = lambda fn, reps: cost[(ctx.rows, ctx.cols, ctx.split)]
     path = str(tmp_path / "t.json")
     choice, times = autotune.tune(ctx, lambda: None, "k1", cache_path=path, timer=timer)
-    # heights first at the default schedule, then schedules at the best height
-    assert choice == {"rows": 16, "cols": 1024, "merge_split": 2} and (ctx.rows, ctx.split) == (16, 2)
-    assert set(times) == {autotune.choice_name(r, s) for r, s in [(32, 4), (16, 4), (16, 1), (16, 2), (16, 8)]}
+    # shapes first at the default schedule, then schedules at the best shape
+    assert choice == {"rows": 16, "cols": 1024, "merge_split": 2}
+    assert (ctx.rows, ctx.cols, ctx.split) == (16, 1024, 2)
+    assert set(times) == {autotune.choice_name(*k) for k in cost}
     # cached: the timer is not consulted again
     ctx2 = FakeCtx()
     choice2, _ = autotune.tune(ctx2, lambda: None, "k1", cache_path=path,
                                timer=lambda fn, reps: pytest.fail("re-timed"))
-    assert choice2 == choice and (ctx2.rows, ctx2.split) == (16, 2)
-    cost[(32, 4)] = 1.0
+    assert choice2 == choice and (ctx2.rows, ctx2.cols, ctx2.split) == (16, 1024, 2)
+    # a narrower tile wins after a forced re-tune
+    cost.update({(32, 512, 4): 1.0, (32, 512, 1): 1.1, (32, 512, 2): 0.9, (32, 512, 8): 1.2})
     choice3, _ = autotune.tune(ctx, lambda: None, "k1", cache_path=path, timer=timer, force=True)
-    assert choice3 == {"rows": 32, "cols": 1024, "merge_split": 1}
+    assert choice3 == {"rows": 32, "cols": 512, "merge_split": 2}
 
 
 def test_size_class_buckets():
@@ -45,8 +49,10 @@ def test_size_class_buckets():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("rows,split", [(16, 4), (32, 4), (32, 1), (32, 2), (32, 8), (16, 1), (16, 8)])
-def test_tile_heights_agree_with_oracle(rows, split):
+@pytest.mark.parametrize("rows,cols,split", [(16, 1024, 4), (32, 1024, 4), (32, 1024, 1), (32, 1024, 2),
+                                             (32, 1024, 8), (16, 1024, 1), (16, 1024, 8), (32, 512, 4),
+                                             (16, 512, 4), (32, 512, 1), (16, 512, 8)])
+def test_tile_shapes_agree_with_oracle(rows, cols, split):
     import torch
 
     import __graft_entry__ as g
@@ -64,6 +70,7 @@ def test_tile_heights_agree_with_oracle(rows, split):
         for conn in (0, 1):
             ctx = ccl.Context(w, h, pitch, conn=conn)
             ctx.set_tile_rows(rows)
+            ctx.set_tile_cols(cols)
             ctx.set_merge_split(split)
             out = ctx.analyze(torch.from_numpy(padded).cuda())
             ctx.fill_holes(8)

@@ -297,8 +297,10 @@ def test_uneven256_full_batch_as_benched(ccl):
     bctx = ccl.BatchContext(len(batch), tot, 2048)
     outs = bctx.new_outputs(shapes, labels=True, fill=True)
     # every tile shape and merge schedule the autotuner can choose
-    for rows, split in [(32, 4), (16, 4), (32, 1), (32, 2), (32, 8), (16, 1), (16, 2), (16, 8)]:
+    for rows, cols, split in [(32, 1024, 4), (16, 1024, 4), (32, 512, 4), (16, 512, 4), (32, 1024, 1),
+                              (32, 1024, 2), (32, 1024, 8), (16, 512, 1), (32, 512, 2), (16, 1024, 8)]:
         bctx.set_tile_rows(rows)
+        bctx.set_tile_cols(cols)
         bctx.set_merge_split(split)
         for _ in range(2):   # the second call replays the cached graph
             bctx.analyze(imgs, outs=outs)
@@ -306,7 +308,7 @@ def test_uneven256_full_batch_as_benched(ccl):
         torch.cuda.synchronize()
         for o, (r, (fmap, ff, fpar)) in zip(outs, refs):
             n = o.n
-            assert o.status() == 0 and n == r["n"], (rows, split)
+            assert o.status() == 0 and n == r["n"], (rows, cols, split)
             np.testing.assert_array_equal(o.fg.cpu().numpy(), r["fg"])
             np.testing.assert_array_equal(o.bg.cpu().numpy(), r["bg"])
             np.testing.assert_array_equal(o.parent[:n].cpu().numpy(), r["parent"])
