@@ -562,11 +562,14 @@ def latency_512(ccl, dev, stream, calls=200, warmup=20):
     of ccl_analyze_static on the same image."""
     import torch
     from paper_2006_09299_gb300 import inputs
+    from paper_2006_09299_gb300 import autotune
     img = inputs.bernoulli(512, 512, 0.5, 1)
     d_img = torch.from_numpy(img).to(dev)
     ctx = ccl.Context(512, 512, 512)
     out = ctx.new_outputs(True, dev)
     sout = ccl.Analysis(512, 512, ccl.node_capacity(512, 512), True, dev)
+    choice, tune_ms = autotune.tune(ctx, lambda: ctx.analyze(d_img, out=out), autotune.size_class([(512, 512)]),
+                                    cache_path=os.path.join(tempfile.mkdtemp(), "tune.json"), reps=20, warmup=5)
 
     def med(fn):
         for _ in range(warmup):
@@ -594,7 +597,9 @@ def latency_512(ccl, dev, stream, calls=200, warmup=20):
             "ccl_analyze_median_us": round(us, 2), "ccl_analyze_min_us": round(us_min, 2),
             "ccl_analyze_gpx_s": round(px / us / 1e3, 3),
             "ccl_analyze_static_median_us": round(sus, 2), "ccl_analyze_static_gpx_s": round(px / sus / 1e3, 3),
-            "note": "each call timed alone (launch latency included); the image and its outputs stay in L2"}
+            "tile": dict(choice, chosen_by="autotuner", tuning_ms={k: round(v, 4) for k, v in tune_ms.items()}),
+            "note": "each call timed alone (launch latency included); the image and its outputs stay in L2; "
+                    "ccl_analyze_static always uses 32 x 1024 tiles"}
 
 
 def batched_vs_plain(ccl, dev, stream, reps=5):
