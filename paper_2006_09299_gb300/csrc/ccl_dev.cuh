@@ -374,7 +374,21 @@ __device__ __forceinline__ void global_union(unsigned long long *gp, uint32_t a,
 
 
 // ------------------------------------------- feature merges in global memory
-// Features are int64 structure-of-arrays: base[f * cap + id].
+// Features are int64 structure-of-arrays: base[f * cap + id]. Two forms of a
+// contribution: global reductions (red: no value returned, the thread does
+// not wait for the L2 round trip; the writer's per-tile flushes, spread over
+// many records), and atomics (the filter's merge, whose flushes from every
+// CTA meet on a few large survivors: measured faster there).
+
+__device__ __forceinline__ void red_add_u64(int64_t *p, unsigned long long v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_min_s64(int64_t *p, long long v) {
+    asm volatile("red.global.min.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_max_s64(int64_t *p, long long v) {
+    asm volatile("red.global.max.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 __device__ __forceinline__ void feat_atomic(int64_t *base, int64_t cap, int id, unsigned long long area,
                                             unsigned long long sx, unsigned long long sy, long long xmin,

@@ -113,17 +113,17 @@ template <int BITS> struct TileHash {
 // record written with atomics already holds its exact ymin: a border node's
 // record starts at its first pixel's row (node ids pass), a spilled record
 // at its root's row, and no pixel of a component lies above its first
-// pixel. So six atomics instead of seven.
+// pixel. So six reductions instead of seven.
 __device__ __forceinline__ void feat_add(int64_t *base, int64_t cap, int id, unsigned long long area,
                                          unsigned long long sx, unsigned long long sy, long long xmin, long long ymin,
                                          long long xmax, long long ymax) {
-    atomicAdd((unsigned long long *)(base + 0 * cap + id), area);
-    atomicMin((long long *)(base + 1 * cap + id), xmin);
-    if (id == 0) atomicMin((long long *)(base + 2 * cap + id), ymin);
-    atomicMax((long long *)(base + 3 * cap + id), xmax);
-    atomicMax((long long *)(base + 4 * cap + id), ymax);
-    atomicAdd((unsigned long long *)(base + 5 * cap + id), sx);
-    atomicAdd((unsigned long long *)(base + 6 * cap + id), sy);
+    red_add_u64(base + 0 * cap + id, area);
+    red_min_s64(base + 1 * cap + id, xmin);
+    if (id == 0) red_min_s64(base + 2 * cap + id, ymin);
+    red_max_s64(base + 3 * cap + id, xmax);
+    red_max_s64(base + 4 * cap + id, ymax);
+    red_add_u64(base + 5 * cap + id, sx);
+    red_add_u64(base + 6 * cap + id, sy);
 }
 
 __device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e) {
