@@ -330,11 +330,20 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
         };
 
         // ---- node ids of the roots; global records of spilled multi-run roots
-        uint32_t info_nx = tid < n_roots ? ri[tid] : 0u;   // one iteration ahead
+        // records loaded two iterations ahead, a border root's union-find
+        // entry one iteration ahead (from the record that has arrived)
+        auto gp_of = [&](uint32_t info) -> uint32_t {
+            return (info >> 17) & 1u ? (uint32_t)B.s.gp[slot0 + ((info >> 18) & 0xFFFu)] : 0u;
+        };
+        uint32_t info_a = tid < n_roots ? ri[tid] : 0u;
+        uint32_t info_b = tid + NT < n_roots ? ri[tid + NT] : 0u;
+        uint32_t gp_a = gp_of(info_a);
         for (int k = tid; k < n_roots; k += NT) {
-            const uint32_t info = info_nx;
-            if (k + NT < n_roots) info_nx = ri[k + NT];
-            const int id = root_id(info);
+            const uint32_t info = info_a, groot = gp_a;
+            info_a = info_b;
+            gp_a = k + NT < n_roots ? gp_of(info_a) : 0u;
+            info_b = k + 2 * NT < n_roots ? ri[k + 2 * NT] : 0u;
+            const int id = !((info >> 17) & 1u) ? root_id(info) : (groot < (uint32_t)n_img ? 0 : B.s.canon[groot]);
             if (k < MAXID) sId[k] = id;
             if (k < n_multi && k >= MAXR && !((info >> 17) & 1u) && id < cap) {
                 d.feat[0 * cap + id] = 0;
@@ -451,22 +460,26 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
             }
             const uint32_t kprev = __shfl_up_sync(FULL, key, 2);
             const bool cont = lane >= 2 && key != 0xFFFFFFFFu && kprev == key;
-            int head = cont ? 0 : lane;   // lane of this chain's first run
+            int xs0 = s;
+            bool cont_next = false;
+            if (__any_sync(FULL, cont)) {   // some run continues a chain
+                int head = cont ? 0 : lane;   // lane of this chain's first run
 #pragma unroll
-            for (int dd = 2; dd < 32; dd <<= 1) {
-                const int hu = __shfl_up_sync(FULL, head, dd);
-                if (lane >= dd) head = max(head, hu);   // even offsets: the same parity
-            }
-#pragma unroll
-            for (int dd = 2; dd < 32; dd <<= 1) {
-                const uint32_t tl = __shfl_up_sync(FULL, len, dd), ts = __shfl_up_sync(FULL, sx, dd);
-                if (lane - dd >= head) {
-                    len += tl;
-                    sx += ts;
+                for (int dd = 2; dd < 32; dd <<= 1) {
+                    const int hu = __shfl_up_sync(FULL, head, dd);
+                    if (lane >= dd) head = max(head, hu);   // even offsets: the same parity
                 }
+#pragma unroll
+                for (int dd = 2; dd < 32; dd <<= 1) {
+                    const uint32_t tl = __shfl_up_sync(FULL, len, dd), ts = __shfl_up_sync(FULL, sx, dd);
+                    if (lane - dd >= head) {
+                        len += tl;
+                        sx += ts;
+                    }
+                }
+                xs0 = __shfl_sync(FULL, s, head);
+                cont_next = __shfl_down_sync(FULL, (int)cont, 2) != 0;
             }
-            const int xs0 = __shfl_sync(FULL, s, head);
-            const bool cont_next = __shfl_down_sync(FULL, (int)cont, 2) != 0;
             if (key != 0xFFFFFFFFu && !(lane < 30 && cont_next)) {
                 const int kk = (int)(key >> 5);
                 // results unused: reductions, the lane does not wait
