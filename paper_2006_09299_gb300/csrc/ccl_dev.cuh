@@ -18,6 +18,7 @@
 //              the component's first pixel in raster order, 0 = exterior.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace ccl {
@@ -491,6 +492,33 @@ __device__ __forceinline__ void hash_flush(const HashTab &H, const ImgDesc *desc
         feat_atomic(filled ? d.filled_feat : d.feat, d.cap, (int)(uint32_t)key, H.area[e], H.sx[e], H.sy[e],
                     H.xmin[e], H.ymin[e], H.xmax[e], H.ymax[e]);
     }
+}
+
+// ------------------------------------------------ programmatic launches
+// Every kernel after the first of an analysis is launched as a programmatic
+// dependent of the kernel before it (launch_dep): its CTAs may be scheduled
+// once every CTA of that kernel has allowed it (pdl_trigger), and they wait
+// (pdl_wait, first thing in every kernel) until that kernel has completed
+// and its memory is visible. The small kernels allow it at their start; the
+// persistent tile kernels when a CTA has no tile left, so that the next
+// kernel's launch overlaps their tail.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // --------------------------------------------------------- host launchers

@@ -89,6 +89,8 @@ struct ImageCursor {
 };
 
 __global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T, int32_t target) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t total = (int64_t)B.n_img + B.s.seg_base[B.n_segs];
     ImageCursor cur;
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total; f += (int64_t)gridDim.x * blockDim.x) {
@@ -127,6 +129,8 @@ __global__ void __launch_bounds__(256) k_fill_map(Batch B, int64_t T, int32_t ta
 // group of equal survivors and only the group's last lane pushes, through
 // the CTA's hash table, then global atomics.
 __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ __align__(16) unsigned char hmem[HT_BYTES];
     const HashTab H = hash_carve(hmem);
     hash_init(H);
@@ -243,6 +247,8 @@ __global__ void __launch_bounds__(256) k_fill_merge(Batch B) {
 // label image of the survivor's colour (-1 in the other). In place is fine
 // (each pixel is read before it is written, by the same thread).
 __global__ void __launch_bounds__(256) k_relabel(Batch B) {
+    pdl_trigger();
+    pdl_wait();
     const ImgDesc &d = B.desc[blockIdx.y];
     if (d.fill_map == nullptr || d.fg == nullptr || d.fg_out == nullptr) return;
     const int64_t npx = (int64_t)d.w * d.h;
@@ -274,7 +280,7 @@ void launch_fill(const Batch &B, int64_t T, int32_t target, const LaunchCfg &c, 
     if (ev) cudaEventRecord(ev[1], st);
     // the merge needs 64 registers per thread, so four of its CTAs fit an
     // SM: one resident wave, one table flush per CTA
-    k_fill_merge<<<4 * c.sms, 256, 0, st>>>(B);
+    launch_dep(k_fill_merge, 4 * c.sms, 256, 0, st, B);
     if (ev) cudaEventRecord(ev[2], st);
 }
 

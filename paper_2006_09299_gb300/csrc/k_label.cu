@@ -36,6 +36,8 @@ namespace ccl {
 constexpr int RI_FG = 16, RI_BORDER = 17, RI_KB = 18, RI_SINGLE = 30;
 
 __global__ void k_prologue(Batch B) {
+    pdl_trigger();
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         *B.s.status = 0;
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r_w = tid / WPR, l_w = tid % WPR;   // this thread's word: row, word in row
+    pdl_wait();   // the prologue's headers and counters are visible
 
     // the rows of a tile: 32 bytes of row r_w at column 32 l_w (16-byte loads
     // that stay inside the row's bytes rounded up to 16, hence its pitch)
@@ -483,6 +486,7 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
             sNb = 0;
         }
     }
+    pdl_trigger();   // no tile left: the next kernel may be scheduled
 }
 
 void launch_prologue(const Batch &B, cudaStream_t st) {
@@ -494,7 +498,7 @@ template <int CONN, int TH, int TW>
 static void launch_label_shape(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     using C = LabelCfg<TH, TW>;
     const int grid = min(B.n_tiles, (1024 / C::NT) * c.sms);
-    k_label<CONN, TH, TW><<<grid, C::NT, label_smem<TH, TW>(), st>>>(B);
+    launch_dep(k_label<CONN, TH, TW>, grid, C::NT, label_smem<TH, TW>(), st, B);
 }
 
 template <int CONN>

@@ -180,6 +180,8 @@ __device__ void merge_perimeter(const Batch &B, const ImgDesc &d, int img, int64
 
 template <int CONN>
 __global__ void k_merge(Batch B) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool ok = true;
     int img = -1;
@@ -201,12 +203,18 @@ __global__ void k_merge(Batch B) {
     if (!ok) set_status(B, B.desc[img], ST_ITER);
 }
 
-// One warp per tile (tiles strided over all warps of the grid): settle the
-// final root of each border root.
-__global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
+// A group of g warps per tile (tiles strided over the groups of the grid;
+// g = 1 when the tiles outnumber the resident warps, up to a whole CTA when
+// there are few), one thread per border root: settle the final root of each
+// border root. (The finds walk chains in L2, so the more of them run side by
+// side the better.)
+__global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B, int g) {
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (NTHREADS / 32);
-    for (int t = blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5); t < B.n_tiles; t += nwarps) {
+    const int gw = blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5);   // global warp
+    const int groups = gridDim.x * (NTHREADS / 32) / g, gt = (gw % g) * 32 + lane;
+    for (int t = gw / g; t < B.n_tiles; t += groups) {
         const TileHdr &h = B.s.thdr[t];
         const int img = h.img;
         const ImgDesc &d = B.desc[img];
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
         const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
         bool ok = true;
         int nfg = 0;
-        for (int kb = lane; kb < nb; kb += 32) {
+        for (int kb = gt; kb < nb; kb += 32 * g) {
             const uint32_t slot = slot0 + kb;
             const uint32_t root = global_find(B.s.gp, slot, &ok);
             if (root != slot) {
@@ -234,6 +242,8 @@ __global__ void __launch_bounds__(NTHREADS) k_resolve(Batch B) {
 
 // Node count of every segment (one tile row: wpr words of the node plane).
 __global__ void __launch_bounds__(SCAN_B) k_scan_count(Batch B) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int sPart[SCAN_B / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
@@ -261,6 +271,8 @@ __global__ void __launch_bounds__(SCAN_B) k_scan_count(Batch B) {
 
 // Exclusive scan of the block sums, one CTA of 1024 threads.
 __global__ void __launch_bounds__(1024) k_scan_blocks(Batch B, int nblk) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int sW[32];
     __shared__ int sCarry;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -289,6 +301,8 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Batch B, int nblk) {
 
 // Segment bases: block base + exclusive scan inside the block.
 __global__ void __launch_bounds__(SCAN_B) k_scan_apply(Batch B) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int sW[SCAN_B / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
@@ -304,18 +318,30 @@ __global__ void __launch_bounds__(SCAN_B) k_scan_apply(Batch B) {
     if (s == B.n_segs - 1) B.s.seg_base[B.n_segs] = base + wbase + ex + v;
 }
 
-// Node id of the component whose first pixel has raster index key.
+// Node id of the component whose first pixel has raster index key: 1 + the
+// nodes of the segments before, + the first-pixel bits before it in its
+// segment (the segment's words read with independent vector loads).
 __device__ __forceinline__ int node_id_of_key(const Batch &B, const ImgDesc &d, int64_t key) {
     const int y = (int)(key / d.w), x = (int)(key - (int64_t)y * d.w);
     const int64_t s = d.seg0 + (int64_t)y * d.TX + (x >> B.log_tw);
     int id = 1 + B.s.seg_base[s] - B.s.seg_base[d.seg0];
     const uint32_t *w = B.s.nodebits + s * B.wpr;
     const int l = (x & (B.tw - 1)) >> 5;
-    for (int k = 0; k < l; ++k) id += __popc(w[k]);
+    const uint4 *w4 = reinterpret_cast<const uint4 *>(w);
+#pragma unroll
+    for (int q = 0; q < WPR_MAX / 4; ++q) {
+        if (4 * q < l) {
+            const uint4 v = w4[q];
+            id += __popc(v.x) + (4 * q + 1 < l ? __popc(v.y) : 0) + (4 * q + 2 < l ? __popc(v.z) : 0) +
+                  (4 * q + 3 < l ? __popc(v.w) : 0);
+        }
+    }
     return id + __popc(w[l] & mask_lt(x & 31));
 }
 
-__global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
+__global__ void __launch_bounds__(NTHREADS) k_canon(Batch B, int g) {
+    pdl_trigger();
+    pdl_wait();
     // image totals
     for (int i = blockIdx.x * NTHREADS + threadIdx.x; i < B.n_img; i += gridDim.x * NTHREADS) {
         const ImgDesc &d = B.desc[i];
@@ -326,15 +352,16 @@ __global__ void __launch_bounds__(NTHREADS) k_canon(Batch B) {
         d.counts[2] = n - nfg;
         if (n > d.cap) set_status(B, d, ST_CAPACITY);
     }
-    // one warp per tile: node ids and initial records of the final roots
-    const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (NTHREADS / 32);
-    for (int t = blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5); t < B.n_tiles; t += nwarps) {
+    // a group of g warps per tile (as in k_resolve), one thread per border
+    // root: node ids and initial records of the final roots
+    const int gw = blockIdx.x * (NTHREADS / 32) + (threadIdx.x >> 5);
+    const int groups = gridDim.x * (NTHREADS / 32) / g, gt = (gw % g) * 32 + (threadIdx.x & 31);
+    for (int t = gw / g; t < B.n_tiles; t += groups) {
         const TileHdr &h = B.s.thdr[t];
         const ImgDesc &d = B.desc[h.img];
         const int nb = B.s.tstat[t].z;
         const uint32_t slot0 = (uint32_t)(B.n_img + h.b);
-        for (int kb = lane; kb < nb; kb += 32) {
+        for (int kb = gt; kb < nb; kb += 32 * g) {
             const uint32_t slot = slot0 + kb;
             const unsigned long long v = B.s.gp[slot];
             if ((uint32_t)v != slot) continue;
@@ -361,26 +388,40 @@ void launch_merge(const Batch &B, cudaStream_t st) {
     if (n == 0) return;
     const int grid = (int)((n + 255) / 256);
     if (B.conn == 0)
-        k_merge<0><<<grid, 256, 0, st>>>(B);
+        launch_dep(k_merge<0>, grid, 256, 0, st, B);
     else
-        k_merge<1><<<grid, 256, 0, st>>>(B);
+        launch_dep(k_merge<1>, grid, 256, 0, st, B);
+}
+
+// Warps per tile for the border-root kernels: the resident warps shared out
+// over the tiles, a power of two from 1 to a CTA's 8.
+static int border_group(const Batch &B, const LaunchCfg &c) {
+    const int64_t warps = (int64_t)8 * c.sms * (NTHREADS / 32);
+    int g = 1;
+    while (g < NTHREADS / 32 && (int64_t)B.n_tiles * g * 2 <= warps) g *= 2;
+    return g;
+}
+
+static int border_grid(const Batch &B, const LaunchCfg &c, int g) {
+    const int64_t blocks = ((int64_t)B.n_tiles * g + NTHREADS / 32 - 1) / (NTHREADS / 32);
+    return (int)max((int64_t)1, min(blocks, (int64_t)8 * c.sms));
 }
 
 void launch_resolve(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    const int blocks = (B.n_tiles + NTHREADS / 32 - 1) / (NTHREADS / 32);
-    k_resolve<<<max(1, min(blocks, 8 * c.sms)), NTHREADS, 0, st>>>(B);
+    const int g = border_group(B, c);
+    launch_dep(k_resolve, border_grid(B, c, g), NTHREADS, 0, st, B, g);
 }
 
 void launch_scan(const Batch &B, cudaStream_t st) {
     const int nblk = (int)((B.n_segs + SCAN_B - 1) / SCAN_B);
-    k_scan_count<<<nblk, SCAN_B, 0, st>>>(B);
-    k_scan_blocks<<<1, 1024, 0, st>>>(B, nblk);
-    k_scan_apply<<<nblk, SCAN_B, 0, st>>>(B);
+    launch_dep(k_scan_count, nblk, SCAN_B, 0, st, B);
+    launch_dep(k_scan_blocks, 1, 1024, 0, st, B, nblk);
+    launch_dep(k_scan_apply, nblk, SCAN_B, 0, st, B);
 }
 
 void launch_canon(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
-    const int blocks = (B.n_tiles + NTHREADS / 32 - 1) / (NTHREADS / 32);
-    k_canon<<<max(1, min(blocks, 8 * c.sms)), NTHREADS, 0, st>>>(B);
+    const int g = border_group(B, c);
+    launch_dep(k_canon, border_grid(B, c, g), NTHREADS, 0, st, B, g);
 }
 
 }  // namespace ccl

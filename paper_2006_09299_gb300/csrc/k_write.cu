@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int l = tid % WPR;   // this thread's word within its rows (word tid and word tid + NT)
+    pdl_wait();   // node ids, merged roots and counters are visible
 
     auto load_planes = [&](const TileHdr &h, PlaneRegs &p) {
         const int64_t rowwords = (int64_t)h.TX * WPR;
@@ -615,12 +616,13 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
         }
         slot = s1;
     }
+    pdl_trigger();   // no tile left: the next kernel may be scheduled
 }
 
 template <int TH, int TW>
 static void launch_write_shape(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
     using C = WriteCfg<TH, TW>;
-    k_write<TH, TW><<<min(B.n_tiles, C::CTAS * c.sms), C::NT, write_smem<TH, TW>(), st>>>(B);
+    launch_dep(k_write<TH, TW>, min(B.n_tiles, C::CTAS * c.sms), C::NT, write_smem<TH, TW>(), st, B);
 }
 
 void launch_write(const Batch &B, const LaunchCfg &c, cudaStream_t st) {
