@@ -295,9 +295,38 @@ class GpuBackend:
         self.capacity_fraction = capacity_fraction
         # frames are staged into their slots' pinned buffers by a few host
         # threads (numpy copies release the interpreter lock), so the
-        # scheduler thread is not limited to one core's copy bandwidth
+        # scheduler thread is not limited to one core's copy bandwidth;
+        # frames the client registered as pinned are copied to the device
+        # directly, without staging
         import concurrent.futures
         self.stager = concurrent.futures.ThreadPoolExecutor(max_workers=stage_threads)
+        self.pinned = {}   # data pointer -> (registered host tensor, nbytes)
+
+    def register_frames(self, frames):
+        """Pin the memory of the client's frame arrays in place (a frame pool
+        that decoders write into); submitted frames that lie in it skip the
+        staging copy. Call unregister_frames before the arrays are freed."""
+        torch = self.torch
+        for f in frames:
+            ptr, n = f.__array_interface__["data"][0], f.nbytes
+            if ptr in self.pinned or not f.flags["C_CONTIGUOUS"]:
+                continue
+            err = torch.cuda.cudart().cudaHostRegister(ptr, n, 0)
+            if int(err) != 0:
+                raise RuntimeError("cudaHostRegister failed (%s)" % (err,))
+            self.pinned[ptr] = (f, n)
+
+    def unregister_frames(self):
+        torch = self.torch
+        torch.cuda.synchronize()
+        for ptr in list(self.pinned):
+            torch.cuda.cudart().cudaHostUnregister(ptr)
+        self.pinned.clear()
+
+    def _direct(self, frame, w):
+        """The frame is registered and its rows are the slot's rows (pitch w)."""
+        return (frame.__array_interface__["data"][0] in self.pinned and frame.flags["C_CONTIGUOUS"]
+                and w % 16 == 0)
 
     @staticmethod
     def size_key(frame):
@@ -328,19 +357,22 @@ class GpuBackend:
     def launch(self, k, batch, fill_threshold):
         torch = self.torch
         st = self.streams[k]
+        direct = [self._direct(r.frame, r.slot.handle[3]) for r in batch]
+
         def stage(r):
             img, out, host, w = r.slot.handle
             host.numpy()[:, :w] = r.frame
-        if len(batch) >= 4:
-            list(self.stager.map(stage, batch))
+        staged = [r for r, dr in zip(batch, direct) if not dr]
+        if len(staged) >= 4:
+            list(self.stager.map(stage, staged))
         else:
-            for r in batch:
+            for r in staged:
                 stage(r)
         with torch.cuda.stream(st):
             imgs, outs = [], []
-            for r in batch:
+            for r, dr in zip(batch, direct):
                 img, out, host, w = r.slot.handle
-                img.copy_(host, non_blocking=True)
+                img.copy_(torch.from_numpy(r.frame) if dr else host, non_blocking=True)
                 imgs.append((img, w))
                 outs.append(out)
             self.ctxs[k].analyze(imgs, outs=outs, stream=st)
