@@ -17,7 +17,8 @@
 //     run in the tile takes its features from that run;
 //   - the tree parent of a node whose first pixel lies in this tile is the
 //     node of the pixel directly above that first pixel (the initial
-//     adjacency of Algorithm 2, kept for the root by Algorithm 3);
+//     adjacency of Algorithm 2, kept for the root by Algorithm 3), set in
+//     the per-root loop by the local root that starts at that pixel;
 //   - the label rows are written 4 pixels per lane, so that each warp
 //     stores 512 contiguous bytes per instruction.
 #include "ccl_dev.cuh"
@@ -493,62 +494,41 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
             }
         }
 
-        // ---- tree: nodes whose first pixel lies in this thread's words;
-        // parent = node of the pixel above (the initial adjacency of
-        // Algorithm 2), from the row above or, on the tile's top row, from the
-        // tile above (or the exterior on the image's top row)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int word = tid + j * NT, r = word / WPR;
-            const uint32_t nbw = sNB[word];
-            uint32_t m = nbw;
-            while (m) {
-                // up to two nodes at a time, their lookups in flight together
-                int bb[2], pq[2];
-                uint32_t pv[2] = {0u, 0u};
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    bb[u] = m ? __ffs(m) - 1 : -1;
-                    if (m) m &= m - 1;
-                    pq[u] = bb[u] >= 0 && r > 0 ? ord_at(r - 1, 32 * l + bb[u]) : -1;
-                    if (pq[u] >= 0) pv[u] = rr[pq[u]];
-                }
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int b = bb[u];
-                    if (b < 0) continue;
-                    const int c = 32 * l + b;
-                    const int id = 1 + sRowSeg[r] + (int)sNBPre[word] + __popc(nbw & mask_lt(b));
-                    int p = 0;
-                    if (r > 0) {
-                        p = id_of(rec_root(pv[u]));
-                    } else if (y0 > 0) {
-                        // the bottom edge cell of the tile above, same column
-                        const uint32_t s2b = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
-                        const uint32_t root = (uint32_t)B.s.gp[s2b];
-                        p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
-                    }
-                    if (id < cap) {
-                        d.parent[id] = p;
-                        if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((sC[word] >> b) & 1u);
-                    } else {
-                        over = true;
-                    }
-                }
-            }
-        }
         __syncthreads();
 
-        // ---- per local root: features (records of multi-run roots; the run
-        // itself for a single-run root)
+        // ---- per local root: the tree and the features. A node's first
+        // pixel is the first pixel of the local root of its component in
+        // the tile that holds it (the node bit there); that root sets the
+        // node's parent = the node of the pixel directly above (the initial
+        // adjacency of Algorithm 2, kept for the root by Algorithm 3), from
+        // the row above or, on the tile's top row, the tile above (or the
+        // exterior on the image's top row). Features: the records of
+        // multi-run roots; the run itself for a single-run root.
         uint32_t fin_nx = tid < n_roots ? ri[tid] : 0u;   // one iteration ahead
         for (int k = tid; k < n_roots; k += NT) {
             const uint32_t info = fin_nx;
             if (k + NT < n_roots) fin_nx = ri[k + NT];
-            if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
             const int idx = info & 0xFFFF, r = idx >> LOG_TW, c = idx & (TW - 1);
             const bool isb = (info >> 17) & 1u;
             const int id = id_of(k);
+            if ((sNB[r * WPR + (c >> 5)] >> (c & 31)) & 1u) {
+                int p = 0;
+                if (r > 0) {
+                    p = id_of(rec_root(rr[ord_at(r - 1, c)]));
+                } else if (y0 > 0) {
+                    // the bottom edge cell of the tile above, same column
+                    const uint32_t s2b = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
+                    const uint32_t root = (uint32_t)B.s.gp[s2b];
+                    p = root < (uint32_t)n_img ? 0 : B.s.canon[root];
+                }
+                if (id < cap) {
+                    d.parent[id] = p;
+                    if (id < d.ncap) B.s.node_fg[d.node0 + id] = (uint8_t)((info >> 16) & 1u);
+                } else {
+                    over = true;
+                }
+            }
+            if (k < n_multi && k >= MAXR) continue;   // accumulated in global memory
             if (id >= cap) continue;
             uint32_t la, lsx, lsy, lx0, lx1, rmask;
             if (k < n_multi) {
