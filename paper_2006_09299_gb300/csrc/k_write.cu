@@ -40,13 +40,13 @@ template <> struct WriteCfg<32, 1024> {
     static constexpr int NT = 512, MAXR = 2048, MAXID = 8192, HASH_BITS = 9, CTAS = 2;
 };
 template <> struct WriteCfg<16, 1024> {
-    static constexpr int NT = 256, MAXR = 1024, MAXID = 3072, HASH_BITS = 8, CTAS = 4;
+    static constexpr int NT = 256, MAXR = 768, MAXID = 2560, HASH_BITS = 8, CTAS = 5;
 };
 template <> struct WriteCfg<32, 512> {
-    static constexpr int NT = 256, MAXR = 1024, MAXID = 3072, HASH_BITS = 8, CTAS = 4;
+    static constexpr int NT = 256, MAXR = 768, MAXID = 2560, HASH_BITS = 8, CTAS = 5;
 };
 template <> struct WriteCfg<16, 512> {
-    static constexpr int NT = 128, MAXR = 512, MAXID = 1536, HASH_BITS = 7, CTAS = 8;
+    static constexpr int NT = 128, MAXR = 320, MAXID = 1280, HASH_BITS = 7, CTAS = 10;
 };
 
 template <int TH, int TW>
