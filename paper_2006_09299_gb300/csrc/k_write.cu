@@ -504,17 +504,28 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
         // the row above or, on the tile's top row, the tile above (or the
         // exterior on the image's top row). Features: the records of
         // multi-run roots; the run itself for a single-run root.
-        uint32_t fin_nx = tid < n_roots ? ri[tid] : 0u;   // one iteration ahead
+        // (root records two iterations ahead; the record of the run above a
+        // node's first pixel one iteration ahead)
+        auto above_rec = [&](uint32_t info) -> uint32_t {
+            const int idx = info & 0xFFFF, r = idx >> LOG_TW, c = idx & (TW - 1);
+            const bool first = (sNB[r * WPR + (c >> 5)] >> (c & 31)) & 1u;
+            return first && r > 0 ? rr[ord_at(r - 1, c)] : 0u;
+        };
+        uint32_t fin_a = tid < n_roots ? ri[tid] : 0u;
+        uint32_t fin_b = tid + NT < n_roots ? ri[tid + NT] : 0u;
+        uint32_t up_a = tid < n_roots ? above_rec(fin_a) : 0u;
         for (int k = tid; k < n_roots; k += NT) {
-            const uint32_t info = fin_nx;
-            if (k + NT < n_roots) fin_nx = ri[k + NT];
+            const uint32_t info = fin_a, up = up_a;
+            fin_a = fin_b;
+            if (k + NT < n_roots) up_a = above_rec(fin_a);
+            if (k + 2 * NT < n_roots) fin_b = ri[k + 2 * NT];
             const int idx = info & 0xFFFF, r = idx >> LOG_TW, c = idx & (TW - 1);
             const bool isb = (info >> 17) & 1u;
             const int id = id_of(k);
             if ((sNB[r * WPR + (c >> 5)] >> (c & 31)) & 1u) {
                 int p = 0;
                 if (r > 0) {
-                    p = id_of(rec_root(rr[ord_at(r - 1, c)]));
+                    p = id_of(rec_root(up));
                 } else if (y0 > 0) {
                     // the bottom edge cell of the tile above, same column
                     const uint32_t s2b = (uint32_t)(n_img + h.b_above) + B.s.edges[h.b_above + tw + c];
@@ -540,13 +551,12 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
                 rmask = sRows[k];
             } else {
                 // the run starting at (r, c) ends where the next run of the
-                // row starts
-                const int qr = ord_at(r, c);
-                int ce = tw;
-                if (qr + 1 < n) {
-                    const int pn = rec_pix(rr[qr + 1]);
-                    if ((pn >> LOG_TW) == r) ce = pn & (TW - 1);
-                }
+                // row starts: the next run-start bit of the row (none beyond
+                // the tile's width), else the row's end
+                int wc = c >> 5;
+                uint32_t m = sE[r * WPR + wc] & ~mask_le(c & 31);
+                while (m == 0u && ++wc < WPR) m = sE[r * WPR + wc];
+                const int ce = m ? 32 * wc + __ffs(m) - 1 : tw;
                 la = (uint32_t)(ce - c);
                 lsx = (uint32_t)((c + ce - 1) * (ce - c) / 2);
                 lsy = (uint32_t)r * la;
