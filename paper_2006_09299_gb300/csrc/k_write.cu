@@ -127,8 +127,10 @@ __device__ __forceinline__ void feat_add(int64_t *base, int64_t cap, int id, uns
     red_add_u64(base + 6 * cap + id, sy);
 }
 
-__device__ __forceinline__ void st_cs_v4(int32_t *p, int a, int b, int c, int e) {
-    asm volatile("st.global.cs.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e));
+// 16-byte label store that does not allocate in L1, which stays free for
+// the run and root records the tile's loops read.
+__device__ __forceinline__ void st_na_v4(int32_t *p, int a, int b, int c, int e) {
+    asm volatile("st.global.L1::no_allocate.v4.s32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(e));
 }
 
 __device__ __forceinline__ void cp_async16_w(void *dst, const void *src) {
@@ -405,8 +407,8 @@ __global__ void __launch_bounds__(WriteCfg<TH, TW>::NT, WriteCfg<TH, TW>::CTAS) 
                             bv[i] = isfg ? -1 : id[i];
                         }
                         if (d.vec) {
-                            st_cs_v4(fgrow + x, fv[0], fv[1], fv[2], fv[3]);
-                            st_cs_v4(bgrow + x, bv[0], bv[1], bv[2], bv[3]);
+                            st_na_v4(fgrow + x, fv[0], fv[1], fv[2], fv[3]);
+                            st_na_v4(bgrow + x, bv[0], bv[1], bv[2], bv[3]);
                         } else {
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
