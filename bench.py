@@ -40,6 +40,7 @@ FILL_T = 64
 LABEL_BYTES_PER_PX = 8      # fg + bg int32 label writes
 IMAGE_BYTES_PER_PX = 1      # uint8 read
 PATH_BYTES_PER_PX = IMAGE_BYTES_PER_PX + LABEL_BYTES_PER_PX
+NODE_BYTES = 7 * 8 + 4      # per node: seven int64 features and the int32 tree parent
 
 
 def log(*a):
@@ -282,6 +283,7 @@ def run_ours(args, rank, world, local_rank):
     # the two tile kernels take nearly equal time: both are reported
     roofline_kernels = [r for r in (kernel_roofline("label"), kernel_roofline("write")) if r]
     path_gbs = PATH_BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+    nodes = sum(o.n for o in outs)
 
     # ---- end to end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(args, ctx, imgs, outs, dev, stream, px)
@@ -319,6 +321,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline_kernels": roofline_kernels,
         "path_roofline": {"bytes_per_pixel": PATH_BYTES_PER_PX, "achieved": round(path_gbs, 1), "peak": peak,
                           "unit": "GB/s", "frac": round(path_gbs / peak, 4)},
+        "full_output_roofline": full_output_roofline(px, nodes, ms, per.get("write"), peak, peak_kind),
         "phase_ms": {k: round(v, 4) for k, v in per.items()},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -487,6 +490,22 @@ def hbm_roofline(kernel, bytes_per_px, px, ms, peak, peak_kind, workload, kernel
     return r
 
 
+def full_output_roofline(px, nodes, path_ms, write_ms, peak, peak_kind):
+    """The second roofline of the measurement plan: every output byte counted,
+    the label images (8 B/px) and the per-node records (60 B/node: seven
+    int64 features and the int32 parent), for the whole path (plus the 1 B/px
+    image read) and for the writer, which produces them."""
+    r = {"bound": "hbm", "bytes_per_pixel": PATH_BYTES_PER_PX, "bytes_per_node": NODE_BYTES, "nodes": int(nodes),
+         "peak": peak, "unit": "GB/s", "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, of measured)"}
+    for key, bpp, ms in (("path", PATH_BYTES_PER_PX, path_ms), ("k_write", LABEL_BYTES_PER_PX, write_ms)):
+        if ms:
+            alg = bpp * px + NODE_BYTES * nodes
+            ach = alg / (ms * 1e-3) / 1e9
+            r[key] = {"algorithmic_bytes": int(alg), "achieved": round(ach, 1), "frac": round(ach / peak, 4),
+                      "ms": round(ms, 4)}
+    return r
+
+
 def single_image_record(ccl, dev, stream, img, w, steps, warmup, name, cpu=True):
     """One image through the single-image API (ccl_create / ccl_analyze /
     ccl_fill_holes): the analysis alone (fg + bg labels, tree, features),
@@ -543,6 +562,7 @@ def single_image_record(ccl, dev, stream, img, w, steps, warmup, name, cpu=True)
                        "outputs": "tree, features, counts (Euler number = n_fg - n_bg + 1); no label images"},
         "launches_per_analysis_fill": launches // 3 if launches else None,
     }
+    rec["full_output_roofline"] = full_output_roofline(px, n_nodes, ms_a, ph["write"], peak, peak_kind)
     if cpu:
         from oracle import reference as orc
         orc.build()

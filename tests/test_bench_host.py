@@ -46,3 +46,15 @@ def test_source_hash_follows_local_headers(tmp_path, monkeypatch):
     assert bench.kernel_source_hash("k.cu") == h0
     (csrc / "dev.cuh").write_text("inline int g(int a) { return a + 1; }\n")
     assert bench.kernel_source_hash("k.cu") != h0          # a header edit makes the record stale
+
+
+def test_full_output_roofline_counts_labels_and_node_records():
+    """9 B/px for the path (8 B/px for the writer) plus 60 B per node."""
+    r = bench.full_output_roofline(px=1000, nodes=10, path_ms=1e-3, write_ms=2e-3, peak=100.0, peak_kind="measured")
+    assert r["bytes_per_node"] == 60 and r["nodes"] == 10
+    assert r["path"]["algorithmic_bytes"] == 9 * 1000 + 60 * 10
+    assert r["k_write"]["algorithmic_bytes"] == 8 * 1000 + 60 * 10
+    # bytes / (ms * 1e-3) / 1e9 GB/s
+    assert r["path"]["achieved"] == pytest.approx(9600 / 1e-6 / 1e9, rel=1e-3)
+    assert r["k_write"]["frac"] == pytest.approx(8600 / 2e-6 / 1e9 / 100.0, rel=1e-3)
+    assert "k_write" not in bench.full_output_roofline(1000, 10, 1e-3, None, 100.0, "measured")
