@@ -134,17 +134,20 @@ __device__ __forceinline__ uint32_t run_find(const uint32_t *par, uint32_t a, bo
     return a;
 }
 
-__device__ __forceinline__ void run_union(uint32_t *par, uint32_t a, uint32_t b, bool *ok) {
+// Returns the root the two sets were joined under (an ancestor of both a
+// and b), where the caller's next union with a may start its find.
+__device__ __forceinline__ uint32_t run_union(uint32_t *par, uint32_t a, uint32_t b, bool *ok) {
     for (int it = 0; it < LOCAL_UNION_LIMIT; ++it) {
         a = run_find_halving(par, a, ok);
         b = run_find_halving(par, b, ok);
-        if (a == b || !*ok) return;
+        if (a == b || !*ok) return a;
         if (a < b) { const uint32_t t = a; a = b; b = t; }
         const uint32_t old = atomicMin(par + a, b);
-        if (old == a) return;
+        if (old == a) return b;
         a = old;
     }
     *ok = false;
+    return a;
 }
 
 // Tile geometry of the labeller: TH rows x TW columns (WPR = TW / 32 words
@@ -339,7 +342,8 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
             const int e_ = run_end<TW>(list, i, n, r, tw);
             int jf, jl;
             touching<CONN, WPR>(sOrd, sE, sC, r - 1, s, e_, v & 1u, tw, &jf, &jl);
-            for (int j = jf; j <= jl; j += 2) run_union(par, (uint32_t)i, (uint32_t)j, &ok);
+            uint32_t ra = (uint32_t)i;   // an ancestor of run i: where the next union's find starts
+            for (int j = jf; j <= jl; j += 2) ra = run_union(par, ra, (uint32_t)j, &ok);
         }
         // the rows of the next tile: their loads complete during the rest of
         // this tile
