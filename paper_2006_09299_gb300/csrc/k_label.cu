@@ -202,9 +202,17 @@ __device__ __forceinline__ void touching(const uint16_t *sOrd, const uint32_t *s
                                          int s, int e, uint32_t c, int tw, int *jf, int *jl) {
     const int adj8 = CONN ? (int)(c ^ 1u) : (int)c;
     const int xa = max(s - adj8, 0), xb = min(e - 1 + adj8, tw - 1);
-    const int oa = ord_at<WPR>(sOrd, sE, rr, xa);
-    const int ob = ord_at<WPR>(sOrd, sE, rr, xb);
-    const uint32_t ca = (sC[rr * WPR + (xa >> 5)] >> (xa & 31)) & 1u;
+    const int wa = rr * WPR + (xa >> 5), wb = rr * WPR + (xb >> 5);
+    const uint32_t ea = sE[wa];
+    const int ba = (int)sOrd[wa];
+    const int oa = ba + __popc(ea & mask_le(xa & 31)) - 1;
+    int ob;
+    if (wb == wa) {
+        ob = ba + __popc(ea & mask_le(xb & 31)) - 1;
+    } else {
+        ob = ord_at<WPR>(sOrd, sE, rr, xb);
+    }
+    const uint32_t ca = (sC[wa] >> (xa & 31)) & 1u;
     *jf = oa + (int)(ca != c);
     *jl = ob;
 }
