@@ -1032,7 +1032,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep4096", choices=["sweep4096", "rings8192", "uneven256", "serve", "paper2048"])
     ap.add_argument("--paper-per-cell", type=int, default=4, help="paper2048: images per density x granularity cell")
-    ap.add_argument("--serve-rates", default="2000,4000,8000,12000,16000,20000,24000,32000")
+    ap.add_argument("--serve-rates", default="2000,4000,8000,16000,24000,28000,32000,36000,40000")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="confirmation window per rate")
     ap.add_argument("--no-serve", action="store_true", help="default line: leave out the serving record")
     ap.add_argument("--serve-staging", action="store_true", help="stage frames through pinned slot buffers")

@@ -206,6 +206,23 @@ ccl_status ccl_create_batched(ccl_ctx **out, int32_t max_images, int64_t max_tot
 ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, int32_t n,
                                ccl_stream_t stream);
 
+/* ccl_analyze_batched for frames that are still in host memory; the paper
+ * has no counterpart: this is the ingest of a serving loop, which receives
+ * frames from decoders or the network in host buffers. host_frames[i] holds
+ * image i's h rows of w bytes, host_pitches[i] bytes apart (>= w); each is
+ * copied asynchronously on the stream into host_descs[i].img (a device
+ * buffer of the caller, rows host_descs[i].pitch bytes apart; one linear
+ * copy when the two pitches are equal, else a 2-D copy) before the
+ * analysis, which then runs as in ccl_analyze_batched. Frames in
+ * page-locked memory (allocated pinned, or registered with cudaHostRegister)
+ * are read by the copy engine directly, so they must stay unchanged until
+ * the stream has passed the copy; other host memory is staged by the CUDA
+ * driver. A null pointer, a non-positive size or a host pitch below w:
+ * CCL_ERR_ARG, with nothing enqueued. */
+ccl_status ccl_analyze_batched_from_host(ccl_ctx *ctx, const ccl_image_desc *host_descs,
+                                         const uint8_t *const *host_frames, const int64_t *host_pitches,
+                                         int32_t n, ccl_stream_t stream);
+
 /* Hole filling for every image of the last batch that has fill buffers. */
 ccl_status ccl_fill_holes_batched(ccl_ctx *ctx, int64_t area_threshold, ccl_stream_t stream);
 

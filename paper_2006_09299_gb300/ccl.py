@@ -52,6 +52,8 @@ SIGNATURES = {
     "ccl_get_counts": (ctypes.c_int, [_p, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "ccl_create_batched": (ctypes.c_int, [ctypes.POINTER(_p), _i32, _i64, _i32]),
     "ccl_analyze_batched": (ctypes.c_int, [_p, ctypes.POINTER(ImageDesc), _i32, _p]),
+    "ccl_analyze_batched_from_host": (ctypes.c_int, [_p, ctypes.POINTER(ImageDesc), ctypes.POINTER(_p),
+                                                     ctypes.POINTER(_i64), _i32, _p]),
     "ccl_fill_holes_batched": (ctypes.c_int, [_p, _i64, _p]),
     "ccl_set_graph_cache": (ctypes.c_int, [_p, _i32]),
     "ccl_set_tile_rows": (ctypes.c_int, [_p, _i32]),
@@ -262,11 +264,26 @@ class BatchContext(_Instrumented):
             outs = self.new_outputs([(w, t.shape[0]) for t, w in images], labels, fill, images[0][0].device)
         descs = (ImageDesc * len(images))()
         for i, ((t, w), o) in enumerate(zip(images, outs)):
-            descs[i] = ImageDesc(t.data_ptr(), int(w), int(t.shape[0]), int(t.stride(0)), _ptr(o.fg), _ptr(o.bg),
-                                 _ptr(o.parent), _ptr(o.features), _ptr(o.counts), o.cap, _ptr(o.fill_map),
-                                 _ptr(o.filled_features), _ptr(o.filled_parent))
+            descs[i] = self.image_desc(t, w, o)
         _check(_lib.ccl_analyze_batched(self._h, descs, len(images), _stream(stream)), "ccl_analyze_batched")
         return outs
+
+    @staticmethod
+    def image_desc(img, w, out):
+        """The descriptor of one image of a batch (device image buffer img,
+        uint8 [h][pitch], and its outputs); callers that reuse buffers keep it."""
+        return ImageDesc(img.data_ptr(), int(w), int(img.shape[0]), int(img.stride(0)), _ptr(out.fg), _ptr(out.bg),
+                         _ptr(out.parent), _ptr(out.features), _ptr(out.counts), out.cap, _ptr(out.fill_map),
+                         _ptr(out.filled_features), _ptr(out.filled_parent))
+
+    def analyze_from_host(self, descs, frames, pitches, stream=None):
+        """descs: ImageDesc array (device buffers); frames: host addresses of
+        the frames (ints), pitches: their row strides in bytes."""
+        n = len(frames)
+        fr = (_p * n)(*frames)
+        pt = (_i64 * n)(*pitches)
+        _check(_lib.ccl_analyze_batched_from_host(self._h, descs, fr, pt, n, _stream(stream)),
+               "ccl_analyze_batched_from_host")
 
     def fill_holes(self, area_threshold, stream=None):
         _check(_lib.ccl_fill_holes_batched(self._h, int(area_threshold), _stream(stream)),

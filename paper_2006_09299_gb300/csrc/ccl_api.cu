@@ -560,6 +560,35 @@ ccl_status ccl_analyze_batched(ccl_ctx *ctx, const ccl_image_desc *host_descs, i
     return run_plan(ctx, P, (cudaStream_t)stream, ctx->graph_cache);
 }
 
+ccl_status ccl_analyze_batched_from_host(ccl_ctx *ctx, const ccl_image_desc *host_descs,
+                                         const uint8_t *const *host_frames, const int64_t *host_pitches,
+                                         int32_t n, ccl_stream_t stream) {
+    if (!ctx || !ctx->batched || !host_descs || !host_frames || !host_pitches || n <= 0) return CCL_ERR_ARG;
+    for (int32_t i = 0; i < n; ++i) {
+        const ccl_image_desc &d = host_descs[i];
+        if (!host_frames[i] || !d.img || d.w <= 0 || d.h <= 0 || host_pitches[i] < d.w) return CCL_ERR_ARG;
+    }
+    // the frames' copies first (the descriptors are checked again by the
+    // plan below, before anything is enqueued from here on)
+    Plan P;
+    ccl_status st = build_plan(host_descs, n, ctx->th, ctx->tw, ctx->hsplit, &P);
+    if (st != CCL_OK) return st;
+    const cudaStream_t cs = (cudaStream_t)stream;
+    for (int32_t i = 0; i < n; ++i) {
+        const ccl_image_desc &d = host_descs[i];
+        // rows laid out alike on both sides: one linear copy (up to the last
+        // row's last pixel); else a 2-D copy of w bytes per row
+        const cudaError_t e =
+            host_pitches[i] == (int64_t)d.pitch
+                ? cudaMemcpyAsync((void *)d.img, host_frames[i], (size_t)(d.h - 1) * (size_t)d.pitch + (size_t)d.w,
+                                  cudaMemcpyHostToDevice, cs)
+                : cudaMemcpy2DAsync((void *)d.img, (size_t)d.pitch, host_frames[i], (size_t)host_pitches[i],
+                                    (size_t)d.w, (size_t)d.h, cudaMemcpyHostToDevice, cs);
+        if (e != cudaSuccess) return CCL_ERR_CUDA;
+    }
+    return run_plan(ctx, P, cs, ctx->graph_cache);
+}
+
 ccl_status ccl_filter_components_batched(ccl_ctx *ctx, int32_t target, int64_t area_threshold,
                                          ccl_stream_t stream) {
     if (!ctx || !ctx->batched) return CCL_ERR_ARG;

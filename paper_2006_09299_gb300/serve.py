@@ -297,7 +297,9 @@ class GpuBackend:
         # threads (numpy copies release the interpreter lock), so the
         # scheduler thread is not limited to one core's copy bandwidth;
         # frames the client registered as pinned are copied to the device
-        # directly, without staging
+        # directly, without staging. Every launch is one library call that
+        # copies the batch's frames and analyses them, from descriptors kept
+        # per slot (the scheduler thread does little per frame)
         import concurrent.futures
         self.stager = concurrent.futures.ThreadPoolExecutor(max_workers=stage_threads)
         self.pinned = {}   # data pointer -> (registered host tensor, nbytes)
@@ -323,10 +325,9 @@ class GpuBackend:
             torch.cuda.cudart().cudaHostUnregister(ptr)
         self.pinned.clear()
 
-    def _direct(self, frame, w):
-        """The frame is registered and its rows are the slot's rows (pitch w)."""
-        return (frame.__array_interface__["data"][0] in self.pinned and frame.flags["C_CONTIGUOUS"]
-                and w % 16 == 0)
+    def _direct(self, frame):
+        """The frame lies in registered memory (rows w bytes apart)."""
+        return frame.__array_interface__["data"][0] in self.pinned and frame.flags["C_CONTIGUOUS"]
 
     @staticmethod
     def size_key(frame):
@@ -349,7 +350,8 @@ class GpuBackend:
         img = torch.empty((h, pitch), dtype=torch.uint8, device=self.dev)
         out = self.ccl.Analysis(w, h, self._cap(key), True, self.dev).alloc_fill()
         host = torch.empty((h, pitch), dtype=torch.uint8).pin_memory()
-        return Slot(key, self.slot_bytes(key), (img, out, host, w))
+        desc = self.ccl.BatchContext.image_desc(img, w, out)
+        return Slot(key, self.slot_bytes(key), (img, out, host, w, desc))
 
     def free_slot(self, slot):
         slot.handle = None
@@ -357,10 +359,10 @@ class GpuBackend:
     def launch(self, k, batch, fill_threshold):
         torch = self.torch
         st = self.streams[k]
-        direct = [self._direct(r.frame, r.slot.handle[3]) for r in batch]
+        direct = [self._direct(r.frame) for r in batch]
 
         def stage(r):
-            img, out, host, w = r.slot.handle
+            img, out, host, w, desc = r.slot.handle
             host.numpy()[:, :w] = r.frame
         staged = [r for r, dr in zip(batch, direct) if not dr]
         if len(staged) >= 4:
@@ -368,17 +370,20 @@ class GpuBackend:
         else:
             for r in staged:
                 stage(r)
-        with torch.cuda.stream(st):
-            imgs, outs = [], []
-            for r, dr in zip(batch, direct):
-                img, out, host, w = r.slot.handle
-                img.copy_(torch.from_numpy(r.frame) if dr else host, non_blocking=True)
-                imgs.append((img, w))
-                outs.append(out)
-            self.ctxs[k].analyze(imgs, outs=outs, stream=st)
-            self.ctxs[k].fill_holes(fill_threshold, stream=st)
-            ev = torch.cuda.Event()
-            ev.record(st)
+        n = len(batch)
+        descs = (self.ccl.ImageDesc * n)()
+        frames, pitches = [0] * n, [0] * n
+        for i, (r, dr) in enumerate(zip(batch, direct)):
+            img, out, host, w, desc = r.slot.handle
+            descs[i] = desc
+            if dr:
+                frames[i], pitches[i] = r.frame.__array_interface__["data"][0], r.frame.strides[0]
+            else:
+                frames[i], pitches[i] = host.data_ptr(), host.stride(0)
+        self.ctxs[k].analyze_from_host(descs, frames, pitches, stream=st)
+        self.ctxs[k].fill_holes(fill_threshold, stream=st)
+        ev = torch.cuda.Event()
+        ev.record(st)
         return ev
 
     def done(self, handle):

@@ -167,6 +167,64 @@ def test_batched_equals_oracle_and_single(ccl):
     bctx.close()
 
 
+def test_batched_from_host_frames_equals_device_inputs(ccl):
+    """ccl_analyze_batched_from_host: frames in host memory, pinned or
+    pageable, with row strides of w (any w), the device buffer's or wider,
+    are copied into device image buffers and analysed; the results equal those of the same images
+    analysed from device memory. A host pitch below w is refused."""
+    batch = inputs.uneven_batch(seed=9, n=12, lo=16, hi=1300)
+    tot = sum(p.shape[0] * w for p, w in batch)
+    ref_ctx = ccl.BatchContext(len(batch), tot, 1300)
+    ref = ref_ctx.analyze([(to_dev(p), w) for p, w in batch], fill=True)
+    ref_ctx.fill_holes(20)
+    ctx = ccl.BatchContext(len(batch), tot, 1300, graph_cache=False)
+    outs = ctx.new_outputs([(w, p.shape[0]) for p, w in batch], fill=True)
+    frames, pitches, keep = [], [], []
+    descs = (ccl.ImageDesc * len(batch))()
+    for i, ((p, w), o) in enumerate(zip(batch, outs)):
+        h = p.shape[0]
+        dev_img = torch.full((h, -(-w // 16) * 16), 77, dtype=torch.uint8, device="cuda")
+        dpitch = dev_img.shape[1]
+        if i % 4 == 0:      # pinned, rows w bytes apart
+            f = torch.empty((h, w), dtype=torch.uint8).pin_memory()
+            f.numpy()[:] = p[:, :w]
+            addr, pitch = f.data_ptr(), w
+        elif i % 4 == 1:    # pageable, rows w bytes apart
+            f = np.ascontiguousarray(p[:, :w])
+            addr, pitch = f.__array_interface__["data"][0], w
+        elif i % 4 == 2:    # pinned, rows laid out as on the device (one linear copy)
+            f = torch.zeros((h, dpitch), dtype=torch.uint8).pin_memory()
+            f.numpy()[:, :w] = p[:, :w]
+            addr, pitch = f.data_ptr(), dpitch
+        else:               # pageable, the padded rows (pitch wider than the device's)
+            f = np.ascontiguousarray(p)
+            addr, pitch = f.__array_interface__["data"][0], p.shape[1]
+        keep += [f, dev_img]
+        descs[i] = ccl.BatchContext.image_desc(dev_img, w, o)
+        frames.append(addr)
+        pitches.append(pitch)
+    for call in range(2):
+        for o in outs:
+            o.fg.fill_(-7)
+        ctx.analyze_from_host(descs, frames, pitches)
+        ctx.fill_holes(20)
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            n = r.n
+            assert o.status() == 0 and o.n == n, call
+            assert torch.equal(o.fg, r.fg) and torch.equal(o.bg, r.bg), call
+            assert torch.equal(o.parent[:n], r.parent[:n]), call
+            assert torch.equal(o.features[:, :n], r.features[:, :n]), call
+            assert torch.equal(o.fill_map[:n], r.fill_map[:n]), call
+            assert torch.equal(o.filled_features[:, :n], r.filled_features[:, :n]), call
+    bad = list(pitches)
+    bad[1] = batch[1][1] - 1
+    with pytest.raises(RuntimeError):
+        ctx.analyze_from_host(descs, frames, bad)
+    ctx.close()
+    ref_ctx.close()
+
+
 def test_capacity_error_reported_on_device(ccl):
     img = inputs.adversarial(64, 64, "checker0")
     d = to_dev(img)
