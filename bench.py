@@ -20,6 +20,7 @@ same workload and metric, a bounded sample of images per step.
 Prints one JSON line (rank 0).
 """
 import argparse
+import contextlib
 import copy
 import hashlib
 import json
@@ -303,12 +304,11 @@ def run_ours(args, rank, world, local_rank):
                                "roofline": hbm_roofline("whole analysis, labels off", IMAGE_BYTES_PER_PX, px, ms_off,
                                                         peak, peak_kind, args.workload),
                                "outputs": "tree, features, counts (Euler number = n_fg - n_bg + 1); no label images"}
+        del offs
         from paper_2006_09299_gb300 import inputs
         extra["rings8192"] = single_image_record(ccl, dev, stream, inputs.rings(), 8192, args.steps, args.warmup,
                                                  "rings8192", cpu=world == 1 and not args.no_cpu_baseline)
         extra["latency_512"] = latency_512(ccl, dev, stream)
-        if not args.no_serve and world == 1:
-            extra["serve"] = serve_sweep(args, confirm_s=args.serve_seconds)
 
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gpixel/s", "n_gpus": world,
@@ -328,6 +328,14 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
     }
     res.update(extra)
+    if args.workload == "sweep4096" and not args.no_extra and not args.no_serve and world == 1:
+        # the serving stream last, with this workload's device buffers and
+        # context released, so that it runs on a device like a server's
+        del outs, d_imgs
+        ctx.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        res["serve"] = serve_sweep(args, confirm_s=args.serve_seconds)
     return res
 
 
@@ -793,9 +801,9 @@ def serve_sweep(args, rates=None, confirm_s=10.0, search_s=2.0):
     is sustained when, over a confirm_s-second window of arrivals, the queue
     stays bounded (its depth never trends up: at most 4 batches waiting in
     95 % of the samples and at most 2 at the end) and every request
-    completes. A short search (search_s seconds per rate) finds the highest
-    candidate; candidates are then confirmed over confirm_s seconds, highest
-    first, until one holds. p50 / p99 latency (arrival to result event) are
+    completes. A short search (search_s seconds per rate, ending after two
+    rates in a row miss) finds the candidates; they are then confirmed over
+    confirm_s seconds, highest first, until one holds. p50 / p99 latency (arrival to result event) are
     those of the confirmed run."""
     import gc
     import torch
@@ -817,9 +825,10 @@ def serve_sweep(args, rates=None, confirm_s=10.0, search_s=2.0):
     rates = rates or [int(x) for x in args.serve_rates.split(",")]
     bound = 4 * args.serve_batch
 
-    def one(rate, seconds):
+    def one(rate, seconds, clocks=False):
         ticks0 = srv.ticks
-        reqs, depth, samples = poisson_run(srv, frames, rate, seconds, seed=rate, depth_samples=True)
+        with ClockSampler(0) if clocks else contextlib.nullcontext() as clk:
+            reqs, depth, samples = poisson_run(srv, frames, rate, seconds, seed=rate, depth_samples=True)
         st = latency_stats(reqs)
         done = [r for r in reqs if r.t_done is not None]
         span = (max(r.t_done for r in done) - min(r.t_arrive for r in done)) if done else 1.0
@@ -829,6 +838,8 @@ def serve_sweep(args, rates=None, confirm_s=10.0, search_s=2.0):
                    queue_max=max(samples) if samples else 0, gpx_s=round(px / span / 1e9, 3),
                    ticks=srv.ticks - ticks0, **st)
         row["sustained"] = depth <= 2 * args.serve_batch and q95 <= bound and len(done) == len(reqs)
+        if clocks:
+            row["clocks"] = clk.summary()
         log("serve", row)
         return row
 
@@ -837,14 +848,16 @@ def serve_sweep(args, rates=None, confirm_s=10.0, search_s=2.0):
     search, confirmed = [], []
     try:
         poisson_run(srv, frames, 1000, 1.0, seed=1)   # warm-up
+        misses = 0
         for rate in rates:
             row = one(rate, search_s)
             search.append(row)
-            if not row["sustained"]:
+            misses = 0 if row["sustained"] else misses + 1
+            if misses == 2:   # two rates in a row over capacity (one miss can be a host stall)
                 break
         cands = [r["rate_hz"] for r in search if r["sustained"]][::-1]
         for rate in cands:
-            row = one(rate, confirm_s)
+            row = one(rate, confirm_s, clocks=True)
             confirmed.append(row)
             if row["sustained"]:
                 break

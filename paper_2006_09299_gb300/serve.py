@@ -117,7 +117,10 @@ class Server:
             req.slot = None
 
     def _admit(self):
-        while self.waiting:
+        # no more admitted than the streams can take plus one batch: under a
+        # burst the rest waits unadmitted, instead of tying up (or allocating)
+        # slots for frames that cannot launch yet
+        while self.waiting and len(self.admitted) < self.max_batch * (self.n_streams + 1):
             r = self.waiting[0]
             key = self.backend.size_key(r.frame)
             if self.free_slots[key]:
@@ -349,9 +352,10 @@ class GpuBackend:
         pitch = -(-w // 16) * 16
         img = torch.empty((h, pitch), dtype=torch.uint8, device=self.dev)
         out = self.ccl.Analysis(w, h, self._cap(key), True, self.dev).alloc_fill()
-        host = torch.empty((h, pitch), dtype=torch.uint8).pin_memory()
         desc = self.ccl.BatchContext.image_desc(img, w, out)
-        return Slot(key, self.slot_bytes(key), (img, out, host, w, desc))
+        # [device image, outputs, pinned staging buffer (allocated on first
+        # use: frames from the registered pool never need it), width, descriptor]
+        return Slot(key, self.slot_bytes(key), [img, out, None, w, desc])
 
     def free_slot(self, slot):
         slot.handle = None
@@ -362,8 +366,10 @@ class GpuBackend:
         direct = [self._direct(r.frame) for r in batch]
 
         def stage(r):
-            img, out, host, w, desc = r.slot.handle
-            host.numpy()[:, :w] = r.frame
+            hd = r.slot.handle
+            if hd[2] is None:
+                hd[2] = torch.empty(tuple(hd[0].shape), dtype=torch.uint8).pin_memory()
+            hd[2].numpy()[:, :hd[3]] = r.frame
         staged = [r for r, dr in zip(batch, direct) if not dr]
         if len(staged) >= 4:
             list(self.stager.map(stage, staged))
