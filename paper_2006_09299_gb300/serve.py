@@ -3,7 +3,9 @@
 Frames (uint8 host arrays of mixed sizes) arrive one by one. The server
   - admits a waiting frame when a resident slot of its size class is free,
     or when the device-memory budget allows a new one (label images, tree,
-    features and the image buffer stay resident per slot and are reused);
+    features and the image buffer stay resident per slot and are reused),
+    while fewer than max_batch x (n_streams + 1) frames are admitted and
+    not yet launched;
   - every tick launches the admitted frames as ONE batched analysis
     (ccl_analyze_batched + ccl_fill_holes_batched) on the next free CUDA
     stream; each stream has its own batched context, so a new tick runs on
