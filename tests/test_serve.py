@@ -65,6 +65,32 @@ def test_batches_respect_max_batch_and_streams():
     assert sorted(rid for _, b in be.launches for rid in b) == list(range(10))
 
 
+def test_a_burst_admits_at_most_one_batch_beyond_the_streams():
+    """Frames beyond what the streams can take plus one batch wait
+    unadmitted: a burst does not allocate a slot for every waiting frame."""
+    be = FakeBackend(delay=0.05)
+    s = Server(be, memory_budget=10**9, max_batch=2, n_streams=1)
+    reqs = [s.submit(np.zeros((2, 3), np.uint8)) for _ in range(20)]
+    s.step()
+    assert len(be.launches) == 1 and len(be.launches[0][1]) == 2
+    assert len(s.admitted) == 2 and len(s.waiting) == 16
+    assert be.alloc == 4          # slots for the launched batch and the next one only
+    released = set()
+    t = time.perf_counter()
+    while time.perf_counter() - t < 5.0:
+        busy = s.step()
+        for r in reqs:
+            if r.done.is_set() and r.rid not in released:
+                s.release(r)      # the client is done with the results: the slot goes back
+                released.add(r.rid)
+        if not busy and len(released) == len(reqs):
+            break
+        time.sleep(0.0005)
+    assert all(r.done.is_set() for r in reqs)
+    assert sorted(rid for _, b in be.launches for rid in b) == list(range(20))
+    assert be.alloc <= 6          # released slots are reused, not allocated per frame
+
+
 def test_continuous_batching_admits_while_in_flight():
     be = FakeBackend(delay=0.02)
     s = Server(be, memory_budget=10**9, max_batch=8, n_streams=2)
