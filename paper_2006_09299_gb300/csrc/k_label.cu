@@ -176,11 +176,11 @@ constexpr size_t label_smem() {
 
 // End column (exclusive) of run i of row r: the next run's start on the same
 // row, else the tile width.
-template <int TW>
+template <int TW, uint32_t LMASK = 0xFFFFu>
 __device__ __forceinline__ int run_end(const uint16_t *list, int i, int n, int r, int tw) {
     constexpr int LOG_TW = TW == 1024 ? 10 : 9;
     if (i + 1 < n) {
-        const int pn = (int)(list[i + 1] >> 1);
+        const int pn = (int)((list[i + 1] & LMASK) >> 1);
         if ((pn >> LOG_TW) == r) return pn & (TW - 1);
     }
     return tw;
@@ -230,6 +230,10 @@ template <int CONN, int TH, int TW>
 __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>::NT) k_label(Batch B) {
     using C = LabelCfg<TH, TW>;
     constexpr int NT = C::NT, NW = C::NW, NPX = C::NPX, KMAX = C::KMAX, WPR = C::WPR, LOG_TW = C::LOG_TW;
+    // tiles of at most 16384 pixels leave bit 15 of a run-list entry free: it
+    // marks a run that a same-colour run of the row below touches
+    constexpr bool BELOW = NPX <= 16384;
+    constexpr uint32_t LMASK = BELOW ? 0x7FFFu : 0xFFFFu;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *par = (uint32_t *)smem;                         // [NPX]
     uint16_t *list = (uint16_t *)(par + NPX);                 // [NPX] pixel index << 1 | colour
@@ -344,14 +348,18 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
         // row-by-row order only matters for the provisional labels, not for
         // the classes.
         for (int i = tid; i < n; i += NT) {
-            const uint32_t v = list[i];
+            const uint32_t v = list[i] & LMASK;
             const int pix = (int)(v >> 1), r = pix >> LOG_TW, s = pix & (TW - 1);
             if (r == 0) continue;
-            const int e_ = run_end<TW>(list, i, n, r, tw);
+            const int e_ = run_end<TW, LMASK>(list, i, n, r, tw);
             int jf, jl;
             touching<CONN, WPR>(sOrd, sE, sC, r - 1, s, e_, v & 1u, tw, &jf, &jl);
             uint32_t ra = (uint32_t)i;   // an ancestor of run i: where the next union's find starts
-            for (int j = jf; j <= jl; j += 2) ra = run_union(par, ra, (uint32_t)j, &ok);
+            for (int j = jf; j <= jl; j += 2) {
+                // run j has a same-colour contact below (read by the closure)
+                if (BELOW) atomicOr((uint32_t *)list + (j >> 1), 1u << (15 + 16 * (j & 1)));
+                ra = run_union(par, ra, (uint32_t)j, &ok);
+            }
         }
         // the rows of the next tile: their loads complete during the rest of
         // this tile
@@ -362,21 +370,25 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
         // roots touching a tile edge are marked; each root is classified (a
         // root is its component's raster-first run, so nothing above touches
         // it: the component has more runs exactly when the root's run touches
-        // a same-colour run of the row below) and counted per (round, warp)
+        // a same-colour run of the row below, which the unions above flagged
+        // in the run list, or a touching range tells on the widest tiles) and
+        // counted per (round, warp)
         int k = 0;
         for (int i0 = 0; i0 < n; i0 += NT, ++k) {
             const int i = i0 + tid;
             bool is_root = false, multi = false;
             if (i < n) {
-                const uint32_t v = list[i];
+                const uint32_t vr = list[i], v = vr & LMASK;
                 const int pix = (int)(v >> 1), r = pix >> LOG_TW, s = pix & (TW - 1);
-                const int e_ = run_end<TW>(list, i, n, r, tw);
+                const int e_ = run_end<TW, LMASK>(list, i, n, r, tw);
                 const uint32_t p = ld_par(par, (uint32_t)i);
                 const uint32_t root = p == (uint32_t)i ? p : run_find(par, p, &ok);
                 if (root != p) par[i] = root;
                 is_root = root == (uint32_t)i;
                 if (r == 0 || r == th - 1 || s == 0 || e_ == tw) atomicOr(&sBrd[root >> 5], 1u << (root & 31));
-                if (is_root && r + 1 < th) {
+                if (BELOW) {
+                    multi = (vr >> 15) & 1u;
+                } else if (is_root && r + 1 < th) {
                     int jf, jl;
                     touching<CONN, WPR>(sOrd, sE, sC, r + 1, s, e_, v & 1u, tw, &jf, &jl);
                     multi = jf <= jl;
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
                 const uint32_t lt = mask_lt(lane);
                 const int kk = multi ? (int)(base & 0xFFFFu) + __popc(bm & lt)
                                      : n_multi + (int)(base >> 16) + __popc(bs & lt);
-                const uint32_t v = list[i];
+                const uint32_t v = list[i] & LMASK;
                 const int pix = (int)(v >> 1);
                 const uint32_t fg = v & 1u;
                 uint32_t info = (uint32_t)pix | (fg << RI_FG) | (multi ? 0u : (1u << RI_SINGLE));
@@ -463,7 +475,7 @@ __global__ void __launch_bounds__(LabelCfg<TH, TW>::NT, 1024 / LabelCfg<TH, TW>:
         for (int i = tid; i < n; i += NT) {
             uint32_t v = ld_par(par, (uint32_t)i);
             if (!(v & PAR_TAG)) v = ld_par(par, v);
-            rr[i] = ((v & PAR_ORD) << 16) | list[i];
+            rr[i] = ((v & PAR_ORD) << 16) | (list[i] & LMASK);
         }
         // (cell i of the loop is also its offset: top, bottom, left, right)
         uint16_t *eg = B.s.edges + h.b;
